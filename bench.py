@@ -1,0 +1,380 @@
+"""Benchmark: multi-reference alignment throughput (images/s) on synthetic particles.
+
+One step is the whole hot path over one stack: reference preparation
+(polar + ring FFT of the K references), alignment of every particle at every
+shift against every reference with and without mirror (polar resampling,
+ring FFT, spectrum contraction, inverse angular FFT, argmax, pose decode)
+and the class-average update.  The workload is the 100,000-particle,
+76 x 76 px, K = 100, 81-shift stack (rings 1..35, mirror on); inputs (2.3 GB)
+are larger than the 129 MB L2, so no flush is needed between steps.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+        [--precision fp32|bf16|fp16] [--n N_IMAGES]
+Under torchrun each rank aligns its own stack (weak scaling); the class sums
+are the one exchange step (all-reduce), then each rank finalises.
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "mra_n100k_L76_K100_shift4"
+METRIC = "MRA images/s at stated K x shifts (BF16+rescore vs FP32 path)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+SM_COUNT_NOMINAL = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--n", type=int, default=None, help="override the stack size (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work (per launch of the dominant kernel)
+# ---------------------------------------------------------------------------
+
+def path_work(info_M, rings):
+    """FP32 flops per (row, reference) pair: contraction 8 sum_f R_f + inverse DFT 5 M log2 M."""
+    M = info_M
+    R = [sum(1 for _, n in rings if n // 2 >= f) for f in range(M // 2 + 1)]
+    return 8 * sum(R), 5 * M * int(round(math.log2(M)))
+
+
+def ring_table(r1, r2, dr):
+    out = []
+    for r in range(r1, r2 + 1, dr):
+        n = 1
+        while n < 2 * math.pi * r:
+            n *= 2
+        out.append((r, n))
+    return out
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    import numpy as np
+    from oracle import mra_oracle as O
+    imgs, refs, cfgd = args
+    cfg = O.MRAConfig(**cfgd)
+    spec = O.reference_spectra(refs, cfg)
+    for im in imgs:
+        O.align_one(im, spec, cfg)
+    return len(imgs)
+
+
+def cpu_baseline(w, n_sample, refs_np, imgs_np):
+    """Time the oracle (as it stands) on n_sample images over a spawn pool of all host cores."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cfgd = dict(L=w.L, first_ring=w.first_ring, last_ring=w.last_ring, ring_step=w.ring_step,
+                shift_range=w.shift_range, shift_step=w.shift_step, mirror=w.mirror)
+    per = max(1, n_sample // cores)
+    jobs = [(imgs_np[i:i + per], refs_np, cfgd) for i in range(0, n_sample, per)]
+    env_keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(processes=min(cores, len(jobs))) as pool:
+            pool.map(_oracle_worker, [(jobs[0][0][:1], refs_np, cfgd)] * min(cores, len(jobs)))  # warm imports
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_worker, jobs))
+            dt = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"value": done / dt, "unit": "images/s", "cores": min(cores, len(jobs)), "kind": "oracle",
+            "sample": f"{done} images of the {w.n}-image stack (K={w.K}, S={int(round(2 * w.shift_range / w.shift_step + 1)) ** 2}, mirror on), FP64 NumPy, one single-threaded worker per core",
+            "seconds": dt}
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    sample = 16
+    refs, imgs, _, _ = synth.make_workload(w, n=max(sample, 64))
+    refs_np = refs.double().numpy()
+    imgs_np = imgs.double().numpy()
+    times = []
+    for step in range(args.warmup + args.steps):
+        r = cpu_baseline(w, sample, refs_np, imgs_np[:sample])
+        if step >= args.warmup:
+            times.append(r)
+    value = statistics.mean(t["value"] for t in times)
+    ms = 1000.0 * w.n / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": w.n, "L": w.L, "K": w.K, "S": 81, "rings": "1..35",
+                       "mirror": 1, "path": "FP64 oracle (explicit DFT sums)",
+                       "step": f"{sample} images per step, scaled to the stack"},
+            "cpu_baseline": {"value": value, "unit": "images/s", "cores": times[-1]["cores"], "kind": "oracle",
+                             "sample": times[-1]["sample"]},
+            "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2011_05755_gb300 as mra
+    from paper_2011_05755_gb300.shard import allreduce_class_sums
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    n = args.n or w.n
+    prec = {"fp32": mra.MRA_FP32, "bf16": mra.MRA_BF16_RESCORE, "fp16": mra.MRA_FP16_RESCORE}[args.precision]
+
+    # CPU baseline first (spawned workers, before heavy GPU work), rank 0 at N = 1 only
+    cpu_line = None
+    refs_np = imgs_np = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r64, i64, _, _ = synth.make_workload(w, n=48)
+        refs_np, imgs_np = r64.double().numpy(), i64.double().numpy()
+        cpu_line = cpu_baseline(w, 48, refs_np, imgs_np)
+
+    # inputs: rank r renders its own particles (weak scaling)
+    wr = synth.Workload(**{**w.__dict__, "seed_particles": w.seed_particles + 100 * rank,
+                           "seed_noise": w.seed_noise + 100 * rank})
+    refs, imgs, _, _ = synth.make_workload(wr, n=n, device=dev)
+    K, L = w.K, w.L
+    torch.cuda.synchronize()
+
+    al = mra.Aligner(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, prec)
+    info = None
+    poses = torch.empty((n, 8), dtype=torch.int32, device=dev)
+    avg = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
+    counts = torch.zeros((K,), dtype=torch.int32, device=dev)
+    sums = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
+    comp = torch.zeros_like(sums)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        al.set_refs(refs, stream)
+        al.align(imgs, poses, stream)
+        if world == 1:
+            mra.mra_average(al.h, imgs, poses, avg, counts, stream)
+        else:
+            sums.zero_()
+            comp.zero_()
+            counts.zero_()
+            mra.mra_class_sums(al.h, imgs, poses, sums, comp, counts, stream)
+            allreduce_class_sums(sums, comp, counts)
+            mra.mra_average_finalize(al.h, sums, comp, counts, avg, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = al.info
+    mra.mra_profile(al.h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = mra.mra_profile_read(al.h)
+    mra.mra_profile(al.h, False)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = n * world / (ms_step / 1000.0)
+
+    # roofline of the dominant kernel (contraction + inverse angular DFT + argmax)
+    rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
+    S = info["S"]
+    f_con, f_ifft = path_work(info["M"], rings)
+    cc = prof["cc"]
+    launches_cc = max(1, cc["launches"])
+    pairs_per_launch = n * S * K * args.steps / launches_cc
+    flops_per_launch = pairs_per_launch * (f_con + f_ifft)
+    avg_launch_s = cc["ms"] / launches_cc / 1000.0
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+    traffic = None
+    try:
+        tr = json.load(open(TRAFFIC_FILE))
+        ent = tr.get("cc_fp32_kernel")
+        if ent and ent.get("source_hash") == source_hash(ent["sources"]):
+            traffic = ent["bytes_per_pair"] * pairs_per_launch
+    except Exception:
+        traffic = None
+    roofline = {"bound": "alu", "kernel": "cc_fp32_kernel (contraction + inverse angular DFT + argmax)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_source": f"FP32 FFMA: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)",
+                "flop_per_pair": f_con + f_ifft, "pairs_per_launch": pairs_per_launch,
+                "avg_launch_ms": avg_launch_s * 1000.0, "share_of_step": cc["ms"] / ms_total}
+    gpu_launches = sum(v["launches"] for v in prof.values())
+
+    # end to end through the host-buffer entry point (pinned memory, copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        h_refs = refs.cpu().pin_memory()
+        h_imgs = imgs.cpu().pin_memory()
+        h_poses = torch.empty((n, 8), dtype=torch.int32).pin_memory()
+        h_avg = torch.zeros((K, L, L), dtype=torch.float32).pin_memory()
+        h_cnt = torch.zeros((K,), dtype=torch.int32).pin_memory()
+        mra.mra_run_host(al.h, h_refs, h_imgs, h_poses, h_avg, h_cnt, stream)  # warm
+        reps = max(1, min(3, args.steps))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mra.mra_run_host(al.h, h_refs, h_imgs, h_poses, h_avg, h_cnt, stream)
+        dt = (time.perf_counter() - t0) / reps
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": n * world / dt, "unit": "images/s",
+               "h2d_bytes_per_step": (h_refs.numel() + h_imgs.numel()) * 4,
+               "d2h_bytes_per_step": h_poses.numel() * 4 + h_avg.numel() * 4 + h_cnt.numel() * 4,
+               "ms_per_step": dt * 1000.0, "api": "mra_run_host"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[args.precision],
+            "data": "synthetic (seeded Gaussian-blob references and particles, SNR 0.1)",
+            "config": {"workload": WORKLOAD, "n_per_gpu": n, "L": L, "K": K, "S": S, "rings": "1..35", "M": info["M"],
+                       "mirror": 1, "path": args.precision,
+                       "step": "set_refs + align + class average",
+                       "l2": "inputs (2.3 GB/GPU) larger than L2; no flush"},
+            "e2e": e2e, "gpu_launches": gpu_launches, "stages": prof, "roofline": roofline,
+            "cpu_baseline": cpu_line, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    al.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+// Polar resampling and ring FFT (Algorithm 1: "convert x_i to polar
+// coordinates with given shift and apply FFT"; for the references the same
+// with no shift, followed by the ring weights of the Sec. 2 quadrature).
+//
+// One CTA handles R consecutive rows (row = image * rows_per_img + shift).
+// Phase 1 writes the bilinear samples of all rows into shared memory; phase 2
+// gives each warp one (row, ring) job: an in-place N/2-point complex FFT of
+// the ring's real samples packed as z_q = x_{2q} + i x_{2q+1}, then the
+// split into the N/2 + 1 real-input bins X(f), written straight into the
+// frequency-major tiled layout [row / 8][bin][row % 8] (FP32 path), or, for
+// the 16-bit tensor-core paths, into the mma.sync A-fragment order: per tile
+// of 8 rows and k-step of 16 rings of one frequency, lane 4g + t of a warp
+// holds {q[g][2t..2t+1], p[g][2t..2t+1], q[g][2t+8..9], p[g][2t+8..9]} with
+// q = Re X - Im X and p = Re X + Im X (rows 0-7 of the MMA are the q values of
+// the 8 tile rows, rows 8-15 their p values).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "dev_util.cuh"
+#include "mra_internal.h"
+#include "ring_fft.cuh"
+
+namespace mra {
+
+__global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a, int R) {
+  extern __shared__ float4 smem_f4[];
+  const int L = g.L, NS = g.NS, M = g.M;
+  const int LL = L * L;
+  const int LLp = (LL + 3) & ~3;
+  const int64_t img = blockIdx.y;
+  const int s0 = blockIdx.x * R;                       // first shift of this CTA
+  const int nrows = min(R, a.rows_per_img - s0);
+  const int64_t row0 = img * a.rows_per_img + s0;
+  float *im = reinterpret_cast<float *>(smem_f4);       // [LLp] the image
+  float2 *tws = reinterpret_cast<float2 *>(im + LLp);    // [M] forward twiddles
+  float *smem = reinterpret_cast<float *>(tws + M);      // [R][NS] samples, then ring FFTs
+  const float c0 = 0.5f * static_cast<float>(L);
+  // 16-bit paths: q / p planes [row][2][NB16] after the samples (zero = padding)
+  const int NB16 = g.KS * 16;
+  unsigned short *planes = reinterpret_cast<unsigned short *>(smem + R * NS);
+  if (a.out16)
+    for (int idx = threadIdx.x; idx < R * NB16; idx += blockDim.x)
+      reinterpret_cast<uint32_t *>(planes)[idx] = 0u;
+  {
+    const float *src = a.imgs + img * LL;
+    if ((LL & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+      for (int i = threadIdx.x; i < LL / 4; i += blockDim.x) reinterpret_cast<float4 *>(im)[i] = __ldg(s4 + i);
+    } else {
+      for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(src + i);
+    }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = g.fwd_tw[i];
+  }
+  __syncthreads();
+
+  // Phase 1: samples x_r(theta_q) = I(c0 + s + r (cos theta_q, sin theta_q)).
+  const int total = nrows * NS;
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int i = idx / NS;
+    const int q = idx - i * NS;
+    float cx = c0, cy = c0;
+    if (a.use_shifts) {
+      const float2 sh = g.shifts[s0 + i];
+      cx += sh.x;
+      cy += sh.y;
+    }
+    const float2 o = g.offs[q];
+    const float v = bilinear_smem(im, L, cx + o.x, cy + o.y);
+    smem[i * NS + q] = v;
+    if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+  }
+  __syncthreads();
+
+  // Phase 2: one warp per (row, ring); largest rings first for balance.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int job = warp; job < nrows * g.NR; job += nwarps) {
+    const int i = job % nrows;
+    const int ring = g.NR - 1 - job / nrows;
+    const int4 rd = g.rings[ring];  // {N, sample offset, natural-bin offset, log2(N/2)}
+    const int N = rd.x, H = N >> 1;
+    float2 *z = reinterpret_cast<float2 *>(smem + i * NS + rd.y);
+    warp_fft_inplace(z, H, rd.w, g.M, tws, lane);
+    const int64_t row = row0 + i;
+    const int wstep = g.M / N;
+    for (int k = lane; k <= H; k += 32) {
+      float2 X = real_split(z, H, k, tws[k * wstep]);
+      const int nb = rd.z + k;
+      if (a.weighted) {
+        const float w = g.bweight[nb];
+        X.x *= w;
+        X.y *= w;
+      }
+      if (a.out) a.out[((row >> 3) * g.NB + g.binpos[nb]) * kTile + (row & 7)] = X;
+      if (a.dbg_spec) a.dbg_spec[row * g.NBIN + nb] = X;
+      if (a.out16) {
+        const int pos = g.binpos16[nb];
+        const float q = X.x - X.y, p = X.x + X.y;
+        planes[(2 * i) * NB16 + pos] = a.fp16 ? __half_as_ushort(__float2half_rn(q))
+                                              : __bfloat16_as_ushort(__float2bfloat16_rn(q));
+        planes[(2 * i + 1) * NB16 + pos] = a.fp16 ? __half_as_ushort(__float2half_rn(p))
+                                                  : __bfloat16_as_ushort(__float2bfloat16_rn(p));
+      }
+    }
+    __syncwarp();
+  }
+
+  // Phase 3 (16-bit paths): fragment-order copy-out, 16 bytes per lane slot.
+  if (a.out16) {
+    __syncthreads();
+    const int per_k = nrows * 4;
+    for (int idx = threadIdx.x; idx < g.KS * per_k; idx += blockDim.x) {
+      const int kk = idx / per_k;
+      const int rem = idx - kk * per_k;
+      const int i = rem >> 2, t = rem & 3;
+      const int64_t row = row0 + i;
+      const int lane16 = 4 * static_cast<int>(row & 7) + t;
+      const unsigned short *qp = planes + (2 * i) * NB16 + kk * 16 + 2 * t;
+      const unsigned short *pp = planes + (2 * i + 1) * NB16 + kk * 16 + 2 * t;
+      uint4 v;
+      v.x = static_cast<uint32_t>(qp[0]) | (static_cast<uint32_t>(qp[1]) << 16);
+      v.y = static_cast<uint32_t>(pp[0]) | (static_cast<uint32_t>(pp[1]) << 16);
+      v.z = static_cast<uint32_t>(qp[8]) | (static_cast<uint32_t>(qp[9]) << 16);
+      v.w = static_cast<uint32_t>(pp[8]) | (static_cast<uint32_t>(pp[9]) << 16);
+      a.out16[((row >> 3) * g.KS + kk) * 32 + lane16] = v;
+    }
+  }
+}
+
+cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
+  if (a.n_imgs <= 0 || a.rows_per_img <= 0) return cudaSuccess;
+  const size_t fixed = (static_cast<size_t>((g.L * g.L + 3) & ~3)) * sizeof(float) + g.M * sizeof(float2);
+  size_t per_row = static_cast<size_t>(g.NS) * sizeof(float);
+  if (a.out16) per_row += static_cast<size_t>(g.KS) * 16 * 2 * sizeof(unsigned short);
+  // two CTAs per SM when the rows fit in ~110 KB, else as many rows as fit in 200 KB
+  int R = static_cast<int>((112640 > fixed ? 112640 - fixed : 0) / per_row);
+  if (R < 1) R = static_cast<int>((204800 - fixed) / per_row);
+  R = R < 1 ? 1 : (R > 8 ? 8 : R);
+  if (R > a.rows_per_img) R = a.rows_per_img;
+  const size_t smem = fixed + per_row * R;
+  static size_t attr_set = 0;
+  if (attr_set < smem) {
+    cudaError_t e = cudaFuncSetAttribute(polar_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  dim3 grid((a.rows_per_img + R - 1) / R, static_cast<unsigned>(a.n_imgs));
+  polar_fft_kernel<<<grid, 256, smem, st>>>(g, a, R);
+  return cudaGetLastError();
+}
+
+}  // namespace mra

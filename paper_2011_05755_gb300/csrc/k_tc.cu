@@ -1,0 +1,485 @@
+// Precision-split path: 16-bit tensor-core spectrum contraction, top-8 row
+// selection, FP32 rescoring of the candidate rows.
+//
+// Contraction on tensor cores.  With q = Re A - Im A, p = Re A + Im A for a
+// particle bin and v = Re B - Im B, u = Re B + Im B for a weighted reference
+// bin, the angular spectrum of a (row, reference) pair at frequency f is
+//     Z(f)     = sum_r q (v + i u),        Z(M - f) = sum_r p (u + i v),
+// i.e. Z = C_u + i C' with C_u = sum conj(A) B and C' = sum A B (the mirror
+// identity).  One mma.sync.m16n8k16 per k-step of 16 rings therefore takes
+// an A operand whose rows 0-7 are the q values of the tile's 8 rows and rows
+// 8-15 their p values, and a B operand whose 8 columns are (v, u) of 4
+// references: the accumulator holds Re/Im Z(f) (q rows) and Im/Re Z(M - f)
+// (p rows) for 8 rows x 4 references.  A tile of 8 rows x 8 references is
+// two such MMAs per k-step.  Operands are BF16 (or FP16), accumulation FP32.
+//
+// The per-pair angular state stays FP32 in shared memory, the inverse DFT
+// and row maxima are FP32, and the 8 rows (reference, shift, mirror) with
+// the largest maxima per image are recomputed from scratch in FP32 by the
+// rescore kernel, whose argmax is the answer.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "../../include/mra.h"
+#include "dev_util.cuh"
+#include "mra_internal.h"
+#include "pair_ifft.cuh"
+#include "ring_fft.cuh"
+#include "tma.cuh"
+
+namespace mra {
+
+__device__ __forceinline__ uint16_t to16(float v, bool fp16) {
+  return fp16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ uint32_t pack16x2(uint16_t lo, uint16_t hi) {
+  return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Reference B fragments: [ref tile of 8][N-block 2][KS][lane 32] x uint2.
+// Lane 4g + t of N-block nb holds column g = (reference 4 nb + g/2, value
+// v if g even else u) at k = 2t, 2t+1 (first word) and 2t+8, 2t+9 (second).
+// ---------------------------------------------------------------------------
+__global__ void refs16_kernel(Geometry g, const float2 *__restrict__ B, int ktiles, uint2 *B16, bool fp16) {
+  const int64_t total = static_cast<int64_t>(ktiles) * g.KS * 64;
+  for (int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int lane = static_cast<int>(idx & 31);
+    const int64_t r = idx >> 5;
+    const int kk = static_cast<int>(r % g.KS);
+    const int nb = static_cast<int>((r / g.KS) & 1);
+    const int kt = static_cast<int>(r / g.KS / 2);
+    const int2 ki = g.ksinfo[kk];
+    const int2 seg = g.fseg[ki.x];
+    const int gi = lane >> 2, t = lane & 3;
+    const int refl = 4 * nb + (gi >> 1), c = gi & 1;
+    const int ks[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+    uint16_t v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int rr = 16 * ki.y + ks[e];
+      float val = 0.f;
+      if (rr < seg.y) {
+        const float2 X = B[(static_cast<int64_t>(kt) * g.NB + seg.x + rr) * kTile + refl];
+        val = c ? (X.x + X.y) : (X.x - X.y);
+      }
+      v[e] = to16(val, fp16);
+    }
+    B16[idx] = make_uint2(pack16x2(v[0], v[1]), pack16x2(v[2], v[3]));
+  }
+}
+
+template <bool FP16>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint4 &a, const uint2 &b) {
+  if constexpr (FP16) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+  } else {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+  }
+}
+
+template <int M, int KT_>
+struct TcShape {
+  static constexpr int RT = kTile, KT = KT_, PAIRS = RT * KT;
+  static constexpr int NBLK = KT / 4;  // MMAs (N-blocks of 4 references) per k-step
+  static constexpr int WARPS = 16, THREADS = 32 * WARPS;
+  static constexpr size_t STATE = static_cast<size_t>(PAIRS) * M * sizeof(float2);
+  static constexpr size_t TW = M * sizeof(float2);
+  static constexpr size_t BARS = WARPS * sizeof(uint64_t);
+  // A: ks_max k-steps x 512 B, then B: NBLK x ks_max x 256 B
+  __host__ __device__ static size_t stage_bytes(int ks_max) {
+    return static_cast<size_t>(ks_max) * 512 + static_cast<size_t>(NBLK) * ks_max * 256;
+  }
+  __host__ __device__ static size_t smem(int ks_max) { return STATE + TW + BARS + WARPS * stage_bytes(ks_max); }
+};
+
+// XOR swizzle matching the epilogue's store pattern (lane 4g + t -> row g, ref t or t + 4).
+template <int KT>
+__device__ __forceinline__ int tc_swz(int p) { return ((p % KT) & 3) + 4 * ((p / KT) & 3); }
+
+template <int M, int KT, bool FP16>
+__global__ void __launch_bounds__(TcShape<M, KT>::THREADS) cc_tc_kernel(Geometry g, TcArgs a) {
+  using Sh = TcShape<M, KT>;
+  constexpr int T = IfftShape<M>::T;
+  constexpr int U = IfftShape<M>::U;
+  extern __shared__ float4 smem_f4[];
+  unsigned char *sbase = reinterpret_cast<unsigned char *>(smem_f4);
+  float2 *Zs = reinterpret_cast<float2 *>(sbase);
+  float2 *tw = reinterpret_cast<float2 *>(sbase + Sh::STATE);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + Sh::STATE + Sh::TW);
+  unsigned char *stage0 = sbase + Sh::STATE + Sh::TW + Sh::BARS;
+  const size_t stage_bytes = Sh::stage_bytes(a.ks_max);
+
+  const int kt = blockIdx.x;
+  const int64_t rt = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < M; i += Sh::THREADS) tw[i] = g.inv_tw[i];
+  if (lane == 0) mbar_init(bars + warp, 1);
+  mbar_init_fence();
+  __syncwarp();
+
+  // ---------------- Phase 1: tensor-core contraction ----------------
+  bool failed = false;
+  {
+    uint4 *stA = reinterpret_cast<uint4 *>(stage0 + warp * stage_bytes);
+    uint2 *stB = reinterpret_cast<uint2 *>(stage0 + warp * stage_bytes + static_cast<size_t>(a.ks_max) * 512);
+    uint64_t *bar = bars + warp;
+    uint32_t phase = 0;
+    bool first_wait = true;
+    const int g8 = lane >> 2, t4 = lane & 3;
+    for (int f = warp; f <= M / 2; f += Sh::WARPS) {
+      const int kb = g.kso[f];
+      const int nks = g.kso[f + 1] - kb;
+      if (lane == 0) {
+        const uint32_t abytes = static_cast<uint32_t>(nks) * 512u;
+        const uint32_t bbytes = static_cast<uint32_t>(nks) * 256u;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, abytes + Sh::NBLK * bbytes);
+        bulk_g2s(stA, a.A16 + (rt * g.KS + kb) * 32, abytes, bar);
+        const int ref0 = kt * KT;
+#pragma unroll
+        for (int nb = 0; nb < Sh::NBLK; ++nb) {
+          const int64_t blk = static_cast<int64_t>(ref0 / kTile) * 2 + (ref0 % kTile) / 4 + nb;
+          bulk_g2s(stB + nb * nks * 32, a.B16 + (blk * g.KS + kb) * 32, bbytes, bar);
+        }
+      }
+      const uint32_t limit = first_wait ? a.first_wait_limit : a.wait_limit;
+      first_wait = false;
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, phase, limit))) {
+        if (lane == 0) atomicOr(a.err, 1);
+        mbar_wait_bounded(bar, phase, a.wait_limit);
+        failed = true;
+        break;
+      }
+      phase ^= 1u;
+      float d[Sh::NBLK][4];
+#pragma unroll
+      for (int nb = 0; nb < Sh::NBLK; ++nb) d[nb][0] = d[nb][1] = d[nb][2] = d[nb][3] = 0.f;
+      for (int j = 0; j < nks; ++j) {
+        const uint4 af = stA[j * 32 + lane];
+#pragma unroll
+        for (int nb = 0; nb < Sh::NBLK; ++nb) mma16816<FP16>(d[nb], af, stB[(nb * nks + j) * 32 + lane]);
+      }
+      // lane (g8, t4): pair (row g8, ref 4 nb + t4) in d[nb]
+#pragma unroll
+      for (int nb = 0; nb < Sh::NBLK; ++nb) {
+        const int pa = g8 * KT + 4 * nb + t4;
+        float2 *za = Zs + pa * M;
+        const int sa = tc_swz<KT>(pa);
+        za[f ^ sa] = make_float2(d[nb][0], d[nb][1]);
+        if (f != 0 && f != M / 2) za[(M - f) ^ sa] = make_float2(d[nb][3], d[nb][2]);
+      }
+      __syncwarp();
+    }
+  }
+  if (__syncthreads_or(failed)) return;
+
+  // ---------------- Phase 2: inverse angular DFT, row maxima ----------------
+  constexpr int GROUPS = Sh::THREADS / T;
+  const int t = threadIdx.x % T;
+  const int S = g.S;
+  for (int p0 = 0; p0 < Sh::PAIRS; p0 += GROUPS) {
+    const int p = p0 + threadIdx.x / T;
+    const bool in_tile = p < Sh::PAIRS;
+    const int pc = in_tile ? p : 0;
+    const int64_t row = rt * Sh::RT + pc / KT;
+    const int ref = kt * KT + pc % KT;
+    const bool valid = in_tile && row < a.rows && ref < a.K;
+    float2 *zp = Zs + pc * M;
+    float2 y[IfftShape<M>::KK][T];
+    pair_ifft<M>(zp, tc_swz<KT>(pc), zp, t, in_tile, tw, y);
+    float vu = -INFINITY, vm = -INFINITY;
+#pragma unroll
+    for (int kk = 0; kk < U / T; ++kk)
+#pragma unroll
+      for (int jj = 0; jj < T; ++jj) {
+        vu = fmaxf(vu, y[kk][jj].x);
+        vm = fmaxf(vm, y[kk][jj].y);
+      }
+#pragma unroll
+    for (int off = T / 2; off > 0; off >>= 1) {
+      vu = fmaxf(vu, __shfl_xor_sync(0xffffffffu, vu, off, T));
+      vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, off, T));
+    }
+    const int64_t img = row / S;
+    const int s = static_cast<int>(row - img * S);
+    if (valid && t == 0) {
+      float *rm = a.rowmax + (img * a.K + ref) * static_cast<int64_t>(S) * 2 + 2 * s;
+      rm[0] = vu;
+      rm[1] = g.mirror ? vm : -INFINITY;
+    }
+    if (a.dbg_cc && valid) {
+      float *d = a.dbg_cc + ((img * a.K + ref) * S + s) * 2 * M;
+#pragma unroll
+      for (int kk = 0; kk < U / T; ++kk)
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+          const int j = ifft_angle<M>(t, kk, jj);
+          d[j] = y[kk][jj].x;
+          d[M + ((j + M / 2) & (M - 1))] = y[kk][jj].y;
+        }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Top-8 rows (reference, shift, mirror) per image by row maximum; ties keep
+// the smaller row index.  One warp per image.
+// ---------------------------------------------------------------------------
+__global__ void top8_kernel(const float *__restrict__ rowmax, int64_t n, int nrows, int *cand) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t img = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
+  if (img >= n) return;
+  float v[kTopRows];
+  int id[kTopRows];
+#pragma unroll
+  for (int e = 0; e < kTopRows; ++e) {
+    v[e] = -INFINITY;
+    id[e] = 0x7fffffff;
+  }
+  const float *rm = rowmax + img * nrows;
+  for (int j = lane; j < nrows; j += 32) {
+    const float x = rm[j];
+    if (x > v[kTopRows - 1]) {
+      v[kTopRows - 1] = x;
+      id[kTopRows - 1] = j;
+#pragma unroll
+      for (int e = kTopRows - 1; e > 0; --e)
+        if (v[e] > v[e - 1]) {
+          const float tv = v[e];
+          v[e] = v[e - 1];
+          v[e - 1] = tv;
+          const int ti = id[e];
+          id[e] = id[e - 1];
+          id[e - 1] = ti;
+        }
+    }
+  }
+  for (int round = 0; round < kTopRows; ++round) {
+    unsigned long long key = (v[0] == -INFINITY) ? 0ull : make_key(v[0], static_cast<uint32_t>(id[0]));
+    unsigned long long best = key;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+      best = o > best ? o : best;
+    }
+    if (lane == 0) cand[img * kTopRows + round] = best ? static_cast<int>(0xffffffffu - static_cast<uint32_t>(best)) : -1;
+    const unsigned win = __ballot_sync(0xffffffffu, best != 0 && key == best);
+    if (best != 0 && lane == __ffs(win) - 1) {
+#pragma unroll
+      for (int e = 0; e < kTopRows - 1; ++e) {
+        v[e] = v[e + 1];
+        id[e] = id[e + 1];
+      }
+      v[kTopRows - 1] = -INFINITY;
+      id[kTopRows - 1] = 0x7fffffff;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 rescore: for each candidate row of an image, resample at its shift,
+// ring-FFT, contract with its reference in FP32, inverse DFT; keep the best
+// (value, smallest index) over the candidates' angles as the argmax key.
+// One CTA per image.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a) {
+  constexpr int T = IfftShape<M>::T;
+  constexpr int U = IfftShape<M>::U;
+  extern __shared__ float4 smem_f4[];
+  const int L = g.L, NS = g.NS, S = g.S;
+  const int LL = L * L;
+  const int LLp = (LL + 3) & ~3;
+  const int64_t img = blockIdx.x;
+  float *im = reinterpret_cast<float *>(smem_f4);
+  float2 *twf = reinterpret_cast<float2 *>(im + LLp);
+  float2 *twi = twf + M;
+  float2 *Z = twi + M;
+  float2 *spec = Z + M;
+  float *samp = reinterpret_cast<float *>(spec + ((g.NBIN + 1) & ~1));
+  const float c0 = 0.5f * static_cast<float>(L);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(a.imgs + img * LL + i);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    twf[i] = g.fwd_tw[i];
+    twi[i] = g.inv_tw[i];
+  }
+  unsigned long long best = 0ull;
+  for (int c = 0; c < kTopRows; ++c) {
+    const int rowid = a.cand[img * kTopRows + c];
+    if (rowid < 0) continue;  // uniform over the CTA
+    const int m = rowid & 1;
+    const int rs = rowid >> 1;
+    const int s = rs % S;
+    const int k = rs / S;
+    __syncthreads();
+    const float2 sh = g.shifts[s];
+    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
+      const float2 o = g.offs[q];
+      samp[q] = bilinear_smem(im, L, c0 + sh.x + o.x, c0 + sh.y + o.y);
+    }
+    __syncthreads();
+    for (int ring = g.NR - 1 - warp; ring >= 0; ring -= 8) {
+      const int4 rd = g.rings[ring];
+      const int N = rd.x, H = N >> 1;
+      float2 *z = reinterpret_cast<float2 *>(samp + rd.y);
+      warp_fft_inplace(z, H, rd.w, M, twf, lane);
+      const int wstep = M / N;
+      for (int kx = lane; kx <= H; kx += 32) spec[rd.z + kx] = real_split(z, H, kx, twf[kx * wstep]);
+      __syncwarp();
+    }
+    __syncthreads();
+    // FP32 contraction with reference k for every frequency
+    const float2 *Bk = a.B + static_cast<int64_t>(k / kTile) * g.NB * kTile + (k % kTile);
+    for (int f = threadIdx.x; f <= M / 2; f += blockDim.x) {
+      float p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;
+      for (int ring = g.NR - 1; ring >= 0; --ring) {
+        const int4 rd = g.rings[ring];
+        if (rd.x / 2 < f) break;
+        const float2 A = spec[rd.z + f];
+        const float2 Bv = __ldg(Bk + static_cast<int64_t>(g.binpos[rd.z + f]) * kTile);
+        p1 = fmaf(A.x, Bv.x, p1);
+        p2 = fmaf(A.y, Bv.y, p2);
+        p3 = fmaf(A.x, Bv.y, p3);
+        p4 = fmaf(A.y, Bv.x, p4);
+      }
+      Z[f] = make_float2((p1 + p2) - (p3 + p4), (p3 - p4) + (p1 - p2));
+      if (f != 0 && f != M / 2) Z[M - f] = make_float2((p1 + p2) + (p3 + p4), (p1 - p2) - (p3 - p4));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int tt = lane % T;
+      const bool owner = lane < T;
+      float2 y[IfftShape<M>::KK][T];
+      pair_ifft<M>(Z, 0, Z, tt, owner, twi, y);
+      float v = -INFINITY;
+      uint32_t ang = 0xffffffffu;
+#pragma unroll
+      for (int kk = 0; kk < U / T; ++kk)
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+          const int j = ifft_angle<M>(tt, kk, jj);
+          const float x = m ? y[kk][jj].y : y[kk][jj].x;
+          const uint32_t aj = m ? static_cast<uint32_t>((j + M / 2) & (M - 1)) : static_cast<uint32_t>(j);
+          if (x > v || (x == v && aj < ang)) {
+            v = x;
+            ang = aj;
+          }
+        }
+      unsigned long long key = owner ? make_key(v, static_cast<uint32_t>(rowid) * M + ang) : 0ull;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+        key = o > key ? o : key;
+      }
+      if (lane == 0 && key > best) best = key;
+    }
+  }
+  if (threadIdx.x == 0) a.best[img] = best;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_refs16(const Geometry &g, const float2 *B, int ktiles, uint2 *B16, bool fp16, cudaStream_t st) {
+  const int64_t total = static_cast<int64_t>(ktiles) * g.KS * 64;
+  const int blocks = static_cast<int>((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  refs16_kernel<<<blocks, 256, 0, st>>>(g, B, ktiles, B16, fp16);
+  return cudaGetLastError();
+}
+
+template <int M, int KT, bool FP16>
+static cudaError_t launch_tc_t(const Geometry &g, const TcArgs &a, cudaStream_t st) {
+  using Sh = TcShape<M, KT>;
+  const size_t smem = Sh::smem(a.ks_max);
+  static size_t attr_set = 0;
+  if (attr_set < smem) {
+    cudaError_t e = cudaFuncSetAttribute(cc_tc_kernel<M, KT, FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  const int64_t row_tiles = (a.rows + Sh::RT - 1) / Sh::RT;
+  if (row_tiles <= 0) return cudaSuccess;
+  dim3 grid((a.K + KT - 1) / KT, static_cast<unsigned>(row_tiles));
+  cc_tc_kernel<M, KT, FP16><<<grid, Sh::THREADS, smem, st>>>(g, a);
+  return cudaGetLastError();
+}
+
+size_t cc_tc_smem(int M, int ks_max) {
+  switch (M) {
+    case 16: return TcShape<16, 8>::smem(ks_max);
+    case 32: return TcShape<32, 8>::smem(ks_max);
+    case 64: return TcShape<64, 8>::smem(ks_max);
+    case 128: return TcShape<128, 8>::smem(ks_max);
+    case 256: return TcShape<256, 8>::smem(ks_max);
+    case 512: return TcShape<512, 4>::smem(ks_max);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStream_t st) {
+#define MRA_TC_CASE(MM, KK) \
+  case MM: return fp16 ? launch_tc_t<MM, KK, true>(g, a, st) : launch_tc_t<MM, KK, false>(g, a, st);
+  switch (g.M) {
+    MRA_TC_CASE(16, 8)
+    MRA_TC_CASE(32, 8)
+    MRA_TC_CASE(64, 8)
+    MRA_TC_CASE(128, 8)
+    MRA_TC_CASE(256, 8)
+    MRA_TC_CASE(512, 4)
+    default: return cudaErrorInvalidValue;
+  }
+#undef MRA_TC_CASE
+}
+
+cudaError_t launch_top8(const float *rowmax, int64_t n, int nrows, int *cand, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  top8_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, st>>>(rowmax, n, nrows, cand);
+  return cudaGetLastError();
+}
+
+size_t rescore_smem(const Geometry &g) {
+  return static_cast<size_t>((g.L * g.L + 3) & ~3) * sizeof(float) + 3 * g.M * sizeof(float2) +
+         static_cast<size_t>((g.NBIN + 1) & ~1) * sizeof(float2) + static_cast<size_t>(g.NS) * sizeof(float);
+}
+
+template <int M>
+static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
+  const size_t smem = rescore_smem(g);
+  static size_t attr_set = 0;
+  if (attr_set < smem) {
+    cudaError_t e =
+        cudaFuncSetAttribute(rescore_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  rescore_kernel<M><<<static_cast<unsigned>(a.n), 256, smem, st>>>(g, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  switch (g.M) {
+    case 16: return launch_rescore_t<16>(g, a, st);
+    case 32: return launch_rescore_t<32>(g, a, st);
+    case 64: return launch_rescore_t<64>(g, a, st);
+    case 128: return launch_rescore_t<128>(g, a, st);
+    case 256: return launch_rescore_t<256>(g, a, st);
+    case 512: return launch_rescore_t<512>(g, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mra
