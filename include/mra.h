@@ -199,6 +199,36 @@ typedef struct {
 int mra_profile(mra_t h, int enable);
 int mra_profile_read(mra_t h, mra_stage_time_t *out);
 
+/* ---- Alignment without device allocation ----
+ * (No counterpart in the paper: this serves callers rather than the method.)
+ * For code that may not call cudaMalloc at all — a framework that owns every
+ * device allocation through its own pool, a latency-critical loop where an
+ * allocation could stall or fail, a process whose free device memory is
+ * promised elsewhere.  Such a caller cannot create a handle (mra_create
+ * allocates), so this call takes the configuration directly and runs the
+ * FP32 alignment of mra_align (precision must be MRA_FP32) with every
+ * intermediate — geometry tables, reference spectra, one chunk of particle
+ * spectra, argmax keys — inside one fixed device array of
+ * MRA_STATIC_SCRATCH_BYTES that the library reserves on each GPU when it is
+ * loaded and keeps until the process exits.  It calls no allocating routine.
+ *   d_refs [K][L][L], d_imgs [n][L][L] float32 and d_poses [n] are the
+ *   caller's device buffers (same meaning as mra_set_refs / mra_align);
+ *   msg (may be NULL) receives an error text of at most msg_len bytes.
+ *   Images are processed in chunks that fit the array; a configuration whose
+ *   tables and reference spectra plus one image do not fit is rejected with
+ *   MRA_EINVAL and a message giving the bytes it would need.
+ *   The first call on a device, with that device current, looks up the
+ *   array's device address (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.
+ *   Host-synchronous (returns after the poses are written; MRA_ETIMEOUT if a
+ *   kernel gave up a bounded wait).  Every call uses the same array, which
+ *   keeps the previous call's contents (each call clears what must start at
+ *   zero); calls whose GPU work overlaps — from two host threads or on two
+ *   streams — race on it and give wrong results. */
+#define MRA_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, const float *d_imgs, int64_t n,
+                     mra_pose_t *d_poses, mra_stream_t stream, char *msg, int32_t msg_len);
+
 /* ---- Stage-level entry points (for parity tests; same kernels as above) ----
  * mra_debug_polar: d_out [n][S][n_samples] float32, ring samples of every
  *   image at every shift (unmirrored), rings in order, q in order.

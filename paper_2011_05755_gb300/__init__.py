@@ -23,7 +23,7 @@ __all__ = [
     "MRA_FP32", "MRA_BF16_RESCORE", "MRA_FP16_RESCORE", "MRAError", "MRAConfig", "MRAInfo", "POSE_FIELDS",
     "library_path", "load_library", "mra_create", "mra_destroy", "mra_last_error", "mra_get_info",
     "mra_set_refs", "mra_align", "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host",
-    "mra_debug_polar", "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "STAGES",
+    "mra_debug_polar", "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "mra_align_static", "STAGES",
     "Aligner", "decode_poses", "EXPORTED_SYMBOLS",
 ]
 
@@ -35,7 +35,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 EXPORTED_SYMBOLS = [
     "mra_create", "mra_destroy", "mra_last_error", "mra_get_info", "mra_set_refs", "mra_align",
     "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host", "mra_debug_polar",
-    "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync",
+    "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "mra_align_static",
 ]
 
 STAGES = ("polar", "refs", "cc", "decode", "average", "rescore", "convert", "unused")
@@ -99,6 +99,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mra_debug_cc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "mra_profile": ([vp, ctypes.c_int], ctypes.c_int),
         "mra_sync": ([vp, vp], ctypes.c_int),
+        "mra_align_static": ([ctypes.POINTER(MRAConfig), vp, i32, vp, i64, vp, vp, ctypes.c_char_p, i32],
+                             ctypes.c_int),
         "mra_profile_read": ([vp, ctypes.POINTER(MRAStageTime)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -229,6 +231,19 @@ def mra_debug_cc(h, imgs, out, stream=None):
 def mra_sync(h, stream=None) -> None:
     """Wait for the handle's work on the stream; raises MRAError(MRA_ETIMEOUT) after a device time-out."""
     _check(load_library().mra_sync(h, _stream(stream)), h)
+
+
+def mra_align_static(refs: torch.Tensor, imgs: torch.Tensor, poses: torch.Tensor, L: int, first_ring: int,
+                     last_ring: int, ring_step: int = 1, shift_range: float = 0.0, shift_step: float = 1.0,
+                     mirror: int = 1, stream=None) -> None:
+    """FP32 alignment that allocates no device memory (no handle); see include/mra.h."""
+    cfg = MRAConfig(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, MRA_FP32, 0)
+    buf = ctypes.create_string_buffer(512)
+    rc = load_library().mra_align_static(ctypes.byref(cfg), _dev_ptr(refs, torch.float32, "refs"), refs.shape[0],
+                                         _dev_ptr(imgs, torch.float32, "imgs"), imgs.shape[0],
+                                         _dev_ptr(poses, torch.int32, "poses"), _stream(stream), buf, len(buf))
+    if rc != MRA_OK:
+        raise MRAError(rc, buf.value.decode())
 
 
 def mra_profile(h, enable: bool) -> None:
