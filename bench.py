@@ -43,10 +43,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32-path comparison run")
     ap.add_argument("--n", type=int, default=None, help="override the stack size (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=60,
+                    help="requests in the serving run (Poisson stream at 0.7 x capacity); 0 skips it")
     return ap.parse_args()
 
 
@@ -249,87 +252,137 @@ def main():
     refs, imgs, _, _ = synth.make_workload(wr, n=n, device=dev)
     K, L = w.K, w.L
     torch.cuda.synchronize()
-
-    al = mra.Aligner(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, prec)
-    info = None
-    poses = torch.empty((n, 8), dtype=torch.int32, device=dev)
-    avg = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
-    counts = torch.zeros((K,), dtype=torch.int32, device=dev)
-    sums = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
-    comp = torch.zeros_like(sums)
+    peaks = {}
+    try:
+        peaks = json.load(open(PEAKS_FILE))
+    except Exception:
+        pass
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
     stream = torch.cuda.current_stream()
 
-    def step():
-        al.set_refs(refs, stream)
-        al.align(imgs, poses, stream)
-        if world == 1:
-            mra.mra_average(al.h, imgs, poses, avg, counts, stream)
+    def run_path(prec_code, label):
+        al = mra.Aligner(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror,
+                         prec_code)
+        poses = torch.empty((n, 8), dtype=torch.int32, device=dev)
+        avg = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
+        counts = torch.zeros((K,), dtype=torch.int32, device=dev)
+        sums = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
+        comp = torch.zeros_like(sums)
+
+        def step():
+            al.set_refs(refs, stream)
+            al.align(imgs, poses, stream)
+            if world == 1:
+                mra.mra_average(al.h, imgs, poses, avg, counts, stream)
+            else:
+                sums.zero_()
+                comp.zero_()
+                counts.zero_()
+                mra.mra_class_sums(al.h, imgs, poses, sums, comp, counts, stream)
+                allreduce_class_sums(sums, comp, counts)
+                mra.mra_average_finalize(al.h, sums, comp, counts, avg, stream)
+
+        for _ in range(args.warmup):
+            step()
+        mra.mra_sync(al.h)
+        info = al.info
+        mra.mra_profile(al.h, True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        mra.mra_sync(al.h)
+        ms_total = ev0.elapsed_time(ev1)
+        prof = mra.mra_profile_read(al.h)
+        mra.mra_profile(al.h, False)
+        if world > 1:
+            t = torch.tensor([ms_total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+        ms_step = ms_total / args.steps
+        S = info["S"]
+        f_con, f_ifft = path_work(info["M"], rings)
+        sm_max = clk.get("sm_max_mhz") or 2070.0
+        alu_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
+        alu_src = (f"FP32 FFMA: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock; "
+                   "an FFMA probe measured 74.3 TFLOP/s)")
+        tpeak = peaks.get("bf16_tflops", 1928.4)
+        tsrc = "bf16_tflops of MEASURED_PEAKS.json (cuBLAS burst), of measured"
+
+        def traffic_for(kernel, units):
+            try:
+                ent = json.load(open(TRAFFIC_FILE)).get(kernel)
+                if ent and ent.get("source_hash") == source_hash(ent["sources"]):
+                    return ent["bytes_per_unit"] * units
+            except Exception:
+                pass
+            return None
+
+        # the contraction / inverse-DFT kernel: one launch per chunk
+        cc = prof["cc"]
+        launches_cc = max(1, cc["launches"])
+        pairs_per_launch = n * S * K * args.steps / launches_cc
+        cc_s = cc["ms"] / launches_cc / 1000.0
+        if prec_code == mra.MRA_FP32:
+            kname = "cc_fp32_kernel"
+            flops = pairs_per_launch * (f_con + f_ifft)
+            cc_line = {"bound": "alu", "kernel": kname + " (FP32 contraction + inverse angular DFT + argmax)",
+                       "achieved": flops / cc_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s", "peak_source": alu_src}
         else:
-            sums.zero_()
-            comp.zero_()
-            counts.zero_()
-            mra.mra_class_sums(al.h, imgs, poses, sums, comp, counts, stream)
-            allreduce_class_sums(sums, comp, counts)
-            mra.mra_average_finalize(al.h, sums, comp, counts, avg, stream)
+            kname = "cc_tc256_kernel" if info["M"] == 256 else "cc_tc_kernel"
+            flops = pairs_per_launch * (f_con + (f_ifft if info["M"] == 256 else 0))
+            cc_line = {"bound": "tensor", "kernel": kname + " (16-bit tensor-core contraction"
+                       + (" and inverse angular DFT" if info["M"] == 256 else " + FP32 inverse DFT") + ", row maxima)",
+                       "achieved": flops / cc_s / 1e12, "peak": tpeak, "unit": "TFLOP/s", "peak_source": tsrc}
+        cc_line.update({"frac": cc_line["achieved"] / cc_line["peak"], "traffic": traffic_for(kname, pairs_per_launch),
+                        "unit_of_work": "(row, reference) pair", "flop_per_unit": flops / pairs_per_launch,
+                        "units_per_launch": pairs_per_launch, "avg_launch_ms": cc_s * 1000.0,
+                        "share_of_step": cc["ms"] / ms_total})
+        # polar resampling + ring FFT: one launch per chunk (plus one for the references)
+        po = prof["polar"]  # particle launches only (the references' launch is the "refs" stage)
+        launches_po = max(1, po["launches"])
+        rows_per_launch = n * S * args.steps / launches_po
+        po_s = po["ms"] / launches_po / 1000.0
+        f_row = sum(2.5 * nr * math.log2(nr) + 9.0 * nr for _, nr in rings)
+        po_line = {"bound": "alu", "kernel": "polar_fft_kernel (bilinear polar resampling + ring FFT)",
+                   "achieved": rows_per_launch * f_row / po_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                   "peak_source": alu_src, "unit_of_work": "(image, shift) row", "flop_per_unit": f_row,
+                   "units_per_launch": rows_per_launch, "avg_launch_ms": po_s * 1000.0,
+                   "traffic": traffic_for("polar_fft_kernel", rows_per_launch),
+                   "share_of_step": po["ms"] / ms_total}
+        po_line["frac"] = po_line["achieved"] / po_line["peak"]
+        roofline, other = (cc_line, po_line) if cc["ms"] >= po["ms"] else (po_line, cc_line)
+        roofline = dict(roofline, other_kernel=other)
+        tensor = None
+        if tensor:
+            roofline["tensor"] = tensor
+        return {"label": label, "al": al, "value": n * world / (ms_step / 1000.0), "ms_step": ms_step,
+                "prof": prof, "roofline": roofline, "clocks": clk, "info": info,
+                "gpu_launches": sum(v["launches"] for v in prof.values())}
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    info = al.info
-    mra.mra_profile(al.h, True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    prof = mra.mra_profile_read(al.h)
-    mra.mra_profile(al.h, False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = n * world / (ms_step / 1000.0)
-
-    # roofline of the dominant kernel (contraction + inverse angular DFT + argmax)
-    rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
+    prec_label = args.precision
+    main_res = run_path(prec, prec_label)
+    cmp_res = None
+    if not args.no_compare and prec != mra.MRA_FP32:
+        cmp_res = run_path(mra.MRA_FP32, "fp32")
+        cmp_res["al"].close()
+    al = main_res["al"]
+    value, ms_step, prof, roofline, clk, info = (main_res[k] for k in ("value", "ms_step", "prof", "roofline",
+                                                                        "clocks", "info"))
     S = info["S"]
-    f_con, f_ifft = path_work(info["M"], rings)
-    cc = prof["cc"]
-    launches_cc = max(1, cc["launches"])
-    pairs_per_launch = n * S * K * args.steps / launches_cc
-    flops_per_launch = pairs_per_launch * (f_con + f_ifft)
-    avg_launch_s = cc["ms"] / launches_cc / 1000.0
-    achieved = flops_per_launch / avg_launch_s / 1e12
-    sm_max = clk.get("sm_max_mhz") or 2070.0
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12
-    traffic = None
-    try:
-        tr = json.load(open(TRAFFIC_FILE))
-        ent = tr.get("cc_fp32_kernel")
-        if ent and ent.get("source_hash") == source_hash(ent["sources"]):
-            traffic = ent["bytes_per_pair"] * pairs_per_launch
-    except Exception:
-        traffic = None
-    roofline = {"bound": "alu", "kernel": "cc_fp32_kernel (contraction + inverse angular DFT + argmax)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_source": f"FP32 FFMA: {nsm} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)",
-                "flop_per_pair": f_con + f_ifft, "pairs_per_launch": pairs_per_launch,
-                "avg_launch_ms": avg_launch_s * 1000.0, "share_of_step": cc["ms"] / ms_total}
-    gpu_launches = sum(v["launches"] for v in prof.values())
+    gpu_launches = main_res["gpu_launches"]
 
     # end to end through the host-buffer entry point (pinned memory, copies inside the timed region)
     e2e = None
@@ -356,6 +409,15 @@ def main():
                "d2h_bytes_per_step": h_poses.numel() * 4 + h_avg.numel() * 4 + h_cnt.numel() * 4,
                "ms_per_step": dt * 1000.0, "api": "mra_run_host"}
 
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        from paper_2011_05755_gb300.serve import run_stream
+        al.close()  # the stream run holds its own handles
+        del imgs
+        torch.cuda.empty_cache()
+        serving = run_stream(args.serve_requests, [0.7], prec, calibration_requests=24)
+        serving["precision"] = args.precision
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
@@ -363,12 +425,18 @@ def main():
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[args.precision],
             "data": "synthetic (seeded Gaussian-blob references and particles, SNR 0.1)",
             "config": {"workload": WORKLOAD, "n_per_gpu": n, "L": L, "K": K, "S": S, "rings": "1..35", "M": info["M"],
-                       "mirror": 1, "path": args.precision,
+                       "mirror": 1, "path": {"fp32": "FP32", "bf16": "BF16 contraction + FP32 rescore of top-8 rows",
+                                             "fp16": "FP16 contraction + FP32 rescore of top-8 rows"}[args.precision],
                        "step": "set_refs + align + class average",
                        "l2": "inputs (2.3 GB/GPU) larger than L2; no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "stages": prof, "roofline": roofline,
-            "cpu_baseline": cpu_line, "clocks": clk,
+            "cpu_baseline": cpu_line, "clocks": clk, "serving": serving,
         }
+        if cmp_res is not None:
+            line["fp32_path"] = {"value": cmp_res["value"], "ms_per_step": cmp_res["ms_step"],
+                                 "speedup_of_headline_path": value / cmp_res["value"],
+                                 "roofline": cmp_res["roofline"], "stages": cmp_res["prof"],
+                                 "gpu_launches": cmp_res["gpu_launches"], "clocks": cmp_res["clocks"]}
         print(json.dumps(line), flush=True)
     al.close()
     if world > 1:

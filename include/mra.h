@@ -132,6 +132,19 @@ int mra_get_info(mra_t h, mra_info_t *info);
  * the handle.  K >= 1.  d_refs may be freed once the stream passes this call. */
 int mra_set_refs(mra_t h, const float *d_refs, int32_t K, mra_stream_t stream);
 
+/* Give handle dst the resident reference spectra of handle src (the output
+ * of mra_set_refs, all precisions the configuration uses) by a device-to-
+ * device copy on `stream`, so that several handles with the same
+ * configuration, each with its own chunk workspace and stream, can align
+ * against one reference set that was transformed once (Algorithm 1's
+ * reference preparation is done per set, not per handle).  The two
+ * configurations must agree in every field but chunk_images (else
+ * MRA_EINVAL); src must hold references (else MRA_ESTATE).  The copy reads
+ * src's buffers: the caller orders it after src's mra_set_refs (same stream,
+ * or an event) and keeps src alive and its references unchanged until the
+ * copy has run.  No paper counterpart: this is serving plumbing. */
+int mra_copy_refs(mra_t dst, mra_t src, mra_stream_t stream);
+
 /* Algorithm 1 per batch: for each image of d_imgs [n][L][L] (float32,
  * device), resample at every shift, ring-FFT, correlate with every reference
  * with and without mirror, inverse angular DFT, and write the argmax pose to
@@ -160,6 +173,18 @@ int mra_class_sums(mra_t h, const float *d_imgs, const mra_pose_t *d_poses, int6
                    float *d_sum, float *d_comp, int32_t *d_counts, mra_stream_t stream);
 int mra_average_finalize(mra_t h, const float *d_sum, const float *d_comp,
                          const int32_t *d_counts, float *d_avg, mra_stream_t stream);
+
+/* Reference refresh for iterative classification (the outer "repeat until
+ * convergence" loop of Algorithm 1): for every class k with d_counts[k] > 0,
+ * d_refs[k] <- (d_refs[k] - mean) / std over the L x L box (std computed
+ * with 1/L^2; a constant image becomes all zero); for a class with count 0
+ * and d_reseed[k] >= 0, d_refs[k] is first replaced by image d_reseed[k] of
+ * d_imgs (then normalised); count 0 and d_reseed[k] < 0 leaves it as is.
+ * d_refs [K][L][L], d_counts [K], d_reseed [K] (device, may be NULL: no
+ * reseeding), d_imgs [n][L][L] (device; may be NULL without reseeding).
+ * Uses the handle's L; K >= 1. */
+int mra_refresh_refs(mra_t h, float *d_refs, const int32_t *d_counts, int32_t K, const int32_t *d_reseed,
+                     const float *d_imgs, int64_t n, mra_stream_t stream);
 
 /* The whole pass from HOST memory, for callers whose data is not on the
  * device: copies h_refs [K][L][L] and h_imgs [n][L][L] in (chunked and

@@ -47,7 +47,8 @@ __all__ = [
     "MRAConfig", "Pose", "ring_table", "angle_count", "shift_list", "bilinear",
     "ring_offsets", "polar_samples", "ring_dft", "ring_weights", "cc_rings",
     "cc_table", "reference_spectra", "particle_spectra", "align", "align_one",
-    "aligned_image", "average", "cc_bruteforce",
+    "aligned_image", "average", "normalize", "refresh_refs", "classify_iteration",
+    "cc_bruteforce",
 ]
 
 
@@ -316,6 +317,49 @@ def average(imgs: np.ndarray, poses: Sequence, K: int, M: int):
     nz = counts > 0
     avg[nz] = sums[nz] / counts[nz, None, None]
     return avg, counts
+
+
+def normalize(img: np.ndarray) -> np.ndarray:
+    """Zero mean, unit standard deviation over the box (``1/L^2`` variance).
+
+    Reading: the classification loop of Algorithm 1 feeds the class averages
+    back as references; their scale is not fixed by the paper, so every new
+    reference is brought to mean 0 and standard deviation 1 (a constant image
+    becomes all zero) so that the cross-correlation maximum compares classes
+    on an equal footing.
+    """
+    x = np.asarray(img, dtype=np.float64)
+    d = x - x.mean()
+    var = float(np.mean(d * d))
+    return d / math.sqrt(var) if var > 0.0 else np.zeros_like(d)
+
+
+def refresh_refs(refs: np.ndarray, avg: np.ndarray, counts: np.ndarray, reseed: Optional[np.ndarray] = None,
+                 imgs: Optional[np.ndarray] = None) -> np.ndarray:
+    """Next references of the classification loop (outer loop of Algorithm 1).
+
+    Class k with ``counts[k] > 0`` becomes ``normalize(avg[k])``; an empty class
+    with ``reseed[k] >= 0`` becomes ``normalize(imgs[reseed[k]])``; any other
+    class keeps ``refs[k]`` unchanged.
+    """
+    out = np.array(refs, dtype=np.float64, copy=True)
+    for k in range(out.shape[0]):
+        if counts[k] > 0:
+            out[k] = normalize(avg[k])
+        elif reseed is not None and reseed[k] >= 0:
+            out[k] = normalize(imgs[reseed[k]])
+    return out
+
+
+def classify_iteration(imgs: np.ndarray, refs: np.ndarray, cfg: MRAConfig, reseed: Optional[np.ndarray] = None):
+    """One pass of the classification loop: align, average, refresh.
+
+    Returns ``(poses, new_refs, counts)``.
+    """
+    poses = align(imgs, refs, cfg)
+    M = angle_count(ring_table(cfg.first_ring, cfg.last_ring, cfg.ring_step))
+    avg, counts = average(imgs, poses, refs.shape[0], M)
+    return poses, refresh_refs(refs, avg, counts, reseed, imgs), counts
 
 
 # ---------------------------------------------------------------------------

@@ -23,7 +23,8 @@ __all__ = [
     "MRA_FP32", "MRA_BF16_RESCORE", "MRA_FP16_RESCORE", "MRAError", "MRAConfig", "MRAInfo", "POSE_FIELDS",
     "library_path", "load_library", "mra_create", "mra_destroy", "mra_last_error", "mra_get_info",
     "mra_set_refs", "mra_align", "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host",
-    "mra_debug_polar", "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "mra_align_static", "STAGES",
+    "mra_debug_polar", "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync",
+    "mra_align_static", "mra_refresh_refs", "mra_copy_refs", "STAGES",
     "Aligner", "decode_poses", "EXPORTED_SYMBOLS",
 ]
 
@@ -35,7 +36,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 EXPORTED_SYMBOLS = [
     "mra_create", "mra_destroy", "mra_last_error", "mra_get_info", "mra_set_refs", "mra_align",
     "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host", "mra_debug_polar",
-    "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "mra_align_static",
+    "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "mra_align_static", "mra_refresh_refs",
+    "mra_copy_refs",
 ]
 
 STAGES = ("polar", "refs", "cc", "decode", "average", "rescore", "convert", "unused")
@@ -89,6 +91,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mra_last_error": ([vp], ctypes.c_char_p),
         "mra_get_info": ([vp, ctypes.POINTER(MRAInfo)], ctypes.c_int),
         "mra_set_refs": ([vp, vp, i32, vp], ctypes.c_int),
+        "mra_copy_refs": ([vp, vp, vp], ctypes.c_int),
         "mra_align": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "mra_average": ([vp, vp, vp, i64, vp, vp, vp], ctypes.c_int),
         "mra_class_sums": ([vp, vp, vp, i64, vp, vp, vp, vp], ctypes.c_int),
@@ -99,6 +102,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mra_debug_cc": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "mra_profile": ([vp, ctypes.c_int], ctypes.c_int),
         "mra_sync": ([vp, vp], ctypes.c_int),
+        "mra_refresh_refs": ([vp, vp, vp, i32, vp, vp, i64, vp], ctypes.c_int),
         "mra_align_static": ([ctypes.POINTER(MRAConfig), vp, i32, vp, i64, vp, vp, ctypes.c_char_p, i32],
                              ctypes.c_int),
         "mra_profile_read": ([vp, ctypes.POINTER(MRAStageTime)], ctypes.c_int),
@@ -169,6 +173,11 @@ def mra_set_refs(h, refs: torch.Tensor, stream=None) -> None:
     _check(load_library().mra_set_refs(h, _dev_ptr(refs, torch.float32, "refs"), refs.shape[0], _stream(stream)), h)
 
 
+def mra_copy_refs(dst, src, stream=None) -> None:
+    """Give handle ``dst`` the resident reference spectra of ``src`` (same configuration)."""
+    _check(load_library().mra_copy_refs(dst, src, _stream(stream)), dst)
+
+
 def mra_align(h, imgs: torch.Tensor, poses: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """Returns poses as an int32 tensor [n, 8] in mra_pose_t layout (see :func:`decode_poses`)."""
     n = imgs.shape[0]
@@ -231,6 +240,17 @@ def mra_debug_cc(h, imgs, out, stream=None):
 def mra_sync(h, stream=None) -> None:
     """Wait for the handle's work on the stream; raises MRAError(MRA_ETIMEOUT) after a device time-out."""
     _check(load_library().mra_sync(h, _stream(stream)), h)
+
+
+def mra_refresh_refs(h, refs: torch.Tensor, counts: torch.Tensor, reseed: Optional[torch.Tensor] = None,
+                     imgs: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Normalise populated classes (and reseed empty ones from chosen images) in place; see include/mra.h."""
+    rs = _dev_ptr(reseed, torch.int32, "reseed") if reseed is not None else None
+    im = _dev_ptr(imgs, torch.float32, "imgs") if imgs is not None else None
+    n = imgs.shape[0] if imgs is not None else 0
+    _check(load_library().mra_refresh_refs(h, _dev_ptr(refs, torch.float32, "refs"),
+                                           _dev_ptr(counts, torch.int32, "counts"), refs.shape[0], rs, im, n,
+                                           _stream(stream)), h)
 
 
 def mra_align_static(refs: torch.Tensor, imgs: torch.Tensor, poses: torch.Tensor, L: int, first_ring: int,
@@ -296,6 +316,10 @@ class Aligner:
     def set_refs(self, refs: torch.Tensor, stream=None):
         mra_set_refs(self.h, refs, stream)
         self.K = refs.shape[0]
+
+    def copy_refs(self, other: "Aligner", stream=None):
+        mra_copy_refs(self.h, other.h, stream)
+        self.K = other.K
 
     def align(self, imgs: torch.Tensor, poses=None, stream=None) -> torch.Tensor:
         return mra_align(self.h, imgs, poses, stream)

@@ -235,6 +235,56 @@ __global__ void avg_finalize_kernel(int LL, const float *sum, const float *comp,
 }
 
 // Requires n >= 1 (the C-ABI layer handles n == 0).
+// Reference refresh: reseed empty classes from a chosen image, then
+// normalise every populated (or reseeded) class to zero mean and unit
+// standard deviation over the box.  One CTA per class; two-pass (mean,
+// then centred second moment) in FP32 with a fixed reduction order.
+__global__ void __launch_bounds__(256) refresh_refs_kernel(int L, float *refs, const int *counts, const int *reseed,
+                                                           const float *imgs, int64_t n) {
+  const int k = blockIdx.x;
+  const int LL = L * L;
+  float *r = refs + static_cast<int64_t>(k) * LL;
+  int src = -1;
+  if (counts[k] <= 0) {
+    src = reseed ? reseed[k] : -1;
+    if (src < 0 || src >= n || !imgs) return;  // leave the class as it is
+    const float *im = imgs + static_cast<int64_t>(src) * LL;
+    for (int i = threadIdx.x; i < LL; i += blockDim.x) r[i] = im[i];
+    __syncthreads();
+  }
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < LL; i += blockDim.x) s += r[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const float mean = red[0] / static_cast<float>(LL);
+  __syncthreads();
+  float q = 0.f;
+  for (int i = threadIdx.x; i < LL; i += blockDim.x) {
+    const float d = r[i] - mean;
+    q = fmaf(d, d, q);
+  }
+  red[threadIdx.x] = q;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const float var = red[0] / static_cast<float>(LL);
+  const float inv = var > 0.f ? rsqrtf(var) : 0.f;
+  for (int i = threadIdx.x; i < LL; i += blockDim.x) r[i] = (r[i] - mean) * inv;
+}
+
+cudaError_t launch_refresh_refs(int L, float *refs, const int *counts, int K, const int *reseed, const float *imgs,
+                                int64_t n, cudaStream_t st) {
+  refresh_refs_kernel<<<K, 256, 0, st>>>(L, refs, counts, reseed, imgs, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_class_sums(const Geometry &g, const float *imgs, const void *poses_v, int64_t n, int K,
                               const AvgWork &w, float *sum, float *comp, int *counts, bool accumulate,
                               cudaStream_t st) {

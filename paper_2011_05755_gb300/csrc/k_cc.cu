@@ -39,7 +39,8 @@ struct CCShape {
   static constexpr int THREADS = 32 * WARPS;
   static constexpr int LANES_PER_SLICE = (RT / 2) * (KT / 2);  // lane = 2 rows x 2 refs
   static constexpr int NSPLIT = 32 / LANES_PER_SLICE;          // bin slices per frequency
-  static constexpr size_t STATE = static_cast<size_t>(PAIRS) * M * sizeof(float2);
+  static constexpr int P = IfftShape<M>::P;                    // float2 per pair buffer
+  static constexpr size_t STATE = static_cast<size_t>(PAIRS) * P * sizeof(float2);
   static constexpr size_t TW = M * sizeof(float2);
   static constexpr size_t BARS = WARPS * sizeof(uint64_t);
   // staging per warp: one frequency segment of the 8-row A tile and the 8-ref B tile
@@ -47,11 +48,12 @@ struct CCShape {
   __host__ __device__ static size_t smem(int seg_max) { return STATE + TW + BARS + WARPS * stage_bytes(seg_max); }
 };
 
-// Bank swizzle of the per-pair spectrum buffers (XOR inside aligned blocks of 16).
-template <int KT>
+// Bank swizzle of the per-pair spectrum buffers (an XOR below T, so the
+// inverse DFT's reads stay one base plus constant offsets).
+template <int M, int KT>
 __device__ __forceinline__ int pair_swz(int p) {
   const int row = p / KT, ref = p % KT;
-  return (row * (KT / 2) + (ref >> 1)) & 15;
+  return (row * (KT / 2) + (ref >> 1)) & (IfftShape<M>::T - 1);
 }
 
 template <int M, int KT>
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(CCShape<M, KT>::THREADS) cc_fp32_kernel(Geomet
   constexpr int U = IfftShape<M>::U;
   extern __shared__ float4 smem_f4[];
   unsigned char *sbase = reinterpret_cast<unsigned char *>(smem_f4);
-  float2 *Zs = reinterpret_cast<float2 *>(sbase);                          // [PAIRS][M]
+  float2 *Zs = reinterpret_cast<float2 *>(sbase);                          // [PAIRS][P]
   float2 *tw = reinterpret_cast<float2 *>(sbase + Sh::STATE);              // [M] inverse twiddles, [k][t]
   uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + Sh::STATE + Sh::TW);
   unsigned char *stage0 = sbase + Sh::STATE + Sh::TW + Sh::BARS;
@@ -148,9 +150,9 @@ __global__ void __launch_bounds__(CCShape<M, KT>::THREADS) cc_fp32_kernel(Geomet
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             const int p = (2 * rp + i) * KT + 2 * kp + j;
-            const int sw = pair_swz<KT>(p);
+            const int sw = pair_swz<M, KT>(p);
             const int q = 2 * i + j;
-            float2 *zp = Zs + p * M;
+            float2 *zp = Zs + p * Sh::P;
             // Z(f) = C_u + i C'
             zp[f ^ sw] = make_float2((p1[q] + p2[q]) - (p3[q] + p4[q]), (p3[q] - p4[q]) + (p1[q] - p2[q]));
             if (f != 0 && f != M / 2)  // Z(M - f) = conj(C_u) + i conj(C')
@@ -174,8 +176,8 @@ __global__ void __launch_bounds__(CCShape<M, KT>::THREADS) cc_fp32_kernel(Geomet
     const int64_t row = rt * Sh::RT + pc / KT;
     const int ref = kt * KT + pc % KT;
     const bool valid = in_tile && row < a.rows && ref < a.K;
-    float2 *zp = Zs + pc * M;
-    const int sw = pair_swz<KT>(pc);
+    float2 *zp = Zs + pc * Sh::P;
+    const int sw = pair_swz<M, KT>(pc);
 
     float2 y[IfftShape<M>::KK][T];
     pair_ifft<M>(zp, sw, zp, t, in_tile, tw, y);
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(CCShape<M, KT>::THREADS) cc_fp32_kernel(Geomet
         if (g.mirror) vmax = fmaxf(vmax, y[kk][jj].y);
       }
 
-    const int64_t img = row / S;
+    const int64_t img = static_cast<uint32_t>(row) / static_cast<uint32_t>(S);  // rows < 2^31 per chunk
     const int s = static_cast<int>(row - img * S);
     if (a.dbg_cc && valid) {
       float *d = a.dbg_cc + ((img * a.K + ref) * S + s) * 2 * M;

@@ -22,7 +22,58 @@
 
 namespace mra {
 
-__global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a, int R) {
+// All (ring, row) jobs of one ring-length class [i0, i1) of a CTA: forward
+// FFT of the packed samples, real split, weights, and the spectrum written in
+// the layout the path needs (FP32 tiled, 16-bit q/p planes, debug).
+template <int H, int R>
+__device__ __forceinline__ int ring_class(const Geometry &g, const PolarArgs &a, float *smem, unsigned short *planes,
+                                          int NB16, const float2 *tws, int i0, int i1, int nrows, int64_t row0,
+                                          int warp, int lane, int nwarps, int first_warp) {
+  constexpr int T = GroupFft<H>::T;
+  constexpr int JPW = 32 / T;  // jobs per warp pass
+  const int njobs = (i1 - i0) * nrows;
+  const int t = lane % T;
+  // warp passes of this class start after the previous class's last pass
+  const int wslot = (warp - first_warp + nwarps) % nwarps;
+  for (int j0 = wslot * JPW; j0 < njobs; j0 += nwarps * JPW) {
+    const int job = j0 + lane / T;
+    const bool active = job < njobs;
+    const int jc = active ? job : j0;
+    const int ring = i0 + jc / nrows;
+    const int i = jc % nrows;
+    const int4 rd = g.rings[ring];  // {N, sample offset, natural-bin offset, log2(N/2)}
+    float2 *z = reinterpret_cast<float2 *>(smem + i * g.NS + rd.y);
+    group_fft<H>(z, t, active, tws, g.M);
+    if (active) {
+      const int wstep = g.M / (2 * H);
+      const int64_t row = row0 + i;
+      for (int k = t; k <= H; k += T) {
+        float2 X = real_split(z, H, k, tws[k * wstep]);
+        const int nb = rd.z + k;
+        if (a.weighted) {
+          const float w = g.bweight[nb];
+          X.x *= w;
+          X.y *= w;
+        }
+        if (a.out) a.out[((row >> 3) * g.NB + g.binpos[nb]) * kTile + (row & 7)] = X;
+        if (a.dbg_spec) a.dbg_spec[row * g.NBIN + nb] = X;
+        if (a.out16) {
+          const int pos16 = g.binpos16[nb];
+          const float q = X.x - X.y, pp = X.x + X.y;
+          planes[(2 * i) * NB16 + pos16] = a.fp16 ? __half_as_ushort(__float2half_rn(q))
+                                                  : __bfloat16_as_ushort(__float2bfloat16_rn(q));
+          planes[(2 * i + 1) * NB16 + pos16] = a.fp16 ? __half_as_ushort(__float2half_rn(pp))
+                                                      : __bfloat16_as_ushort(__float2bfloat16_rn(pp));
+        }
+      }
+    }
+    __syncwarp();
+  }
+  return (first_warp + (njobs + JPW - 1) / JPW) % nwarps;  // first warp of the next class
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a) {
   extern __shared__ float4 smem_f4[];
   const int L = g.L, NS = g.NS, M = g.M;
   const int LL = L * L;
@@ -54,55 +105,52 @@ __global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a,
   __syncthreads();
 
   // Phase 1: samples x_r(theta_q) = I(c0 + s + r (cos theta_q, sin theta_q)).
-  const int total = nrows * NS;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int i = idx / NS;
-    const int q = idx - i * NS;
-    float cx = c0, cy = c0;
-    if (a.use_shifts) {
+  float cx[R], cy[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    cx[i] = c0;
+    cy[i] = c0;
+    if (a.use_shifts && i < nrows) {
       const float2 sh = g.shifts[s0 + i];
-      cx += sh.x;
-      cy += sh.y;
+      cx[i] += sh.x;
+      cy[i] += sh.y;
     }
+  }
+  for (int q = threadIdx.x; q < NS; q += blockDim.x) {
     const float2 o = g.offs[q];
-    const float v = bilinear_smem(im, L, cx + o.x, cy + o.y);
-    smem[i * NS + q] = v;
-    if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      if (i < nrows) {
+        const float v = bilinear_smem(im, L, cx[i] + o.x, cy[i] + o.y);
+        smem[i * NS + q] = v;
+        if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+      }
+    }
   }
   __syncthreads();
 
-  // Phase 2: one warp per (row, ring); largest rings first for balance.
+  // Phase 2: ring FFTs.  Rings of equal length form a contiguous class; the
+  // (ring, row) jobs of a class are spread over the warps, 32 / T jobs per
+  // warp, each transformed by a group of T threads (group_fft).
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int job = warp; job < nrows * g.NR; job += nwarps) {
-    const int i = job % nrows;
-    const int ring = g.NR - 1 - job / nrows;
-    const int4 rd = g.rings[ring];  // {N, sample offset, natural-bin offset, log2(N/2)}
-    const int N = rd.x, H = N >> 1;
-    float2 *z = reinterpret_cast<float2 *>(smem + i * NS + rd.y);
-    warp_fft_inplace(z, H, rd.w, g.M, tws, lane);
-    const int64_t row = row0 + i;
-    const int wstep = g.M / N;
-    for (int k = lane; k <= H; k += 32) {
-      float2 X = real_split(z, H, k, tws[k * wstep]);
-      const int nb = rd.z + k;
-      if (a.weighted) {
-        const float w = g.bweight[nb];
-        X.x *= w;
-        X.y *= w;
-      }
-      if (a.out) a.out[((row >> 3) * g.NB + g.binpos[nb]) * kTile + (row & 7)] = X;
-      if (a.dbg_spec) a.dbg_spec[row * g.NBIN + nb] = X;
-      if (a.out16) {
-        const int pos = g.binpos16[nb];
-        const float q = X.x - X.y, p = X.x + X.y;
-        planes[(2 * i) * NB16 + pos] = a.fp16 ? __half_as_ushort(__float2half_rn(q))
-                                              : __bfloat16_as_ushort(__float2bfloat16_rn(q));
-        planes[(2 * i + 1) * NB16 + pos] = a.fp16 ? __half_as_ushort(__float2half_rn(p))
-                                                  : __bfloat16_as_ushort(__float2bfloat16_rn(p));
-      }
+  int fw = 0;  // warp that takes the first pass of the next class
+  for (int i1 = g.NR; i1 > 0;) {
+    const int H = g.rings[i1 - 1].x >> 1;
+    int i0 = i1 - 1;
+    while (i0 > 0 && (g.rings[i0 - 1].x >> 1) == H) --i0;
+#define MRA_RING_CLASS(HH) \
+  fw = ring_class<HH, R>(g, a, smem, planes, NB16, tws, i0, i1, nrows, row0, warp, lane, nwarps, fw)
+    switch (H) {
+      case 4: MRA_RING_CLASS(4); break;
+      case 8: MRA_RING_CLASS(8); break;
+      case 16: MRA_RING_CLASS(16); break;
+      case 32: MRA_RING_CLASS(32); break;
+      case 64: MRA_RING_CLASS(64); break;
+      case 128: MRA_RING_CLASS(128); break;
+      default: MRA_RING_CLASS(256); break;
     }
-    __syncwarp();
+#undef MRA_RING_CLASS
+    i1 = i0;
   }
 
   // Phase 3 (16-bit paths): fragment-order copy-out, 16 bytes per lane slot.
@@ -127,6 +175,20 @@ __global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a,
   }
 }
 
+template <int R>
+static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t smem, cudaStream_t st) {
+  static size_t attr_set = 0;
+  if (attr_set < smem) {
+    cudaError_t e = cudaFuncSetAttribute(polar_fft_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  dim3 grid((a.rows_per_img + R - 1) / R, static_cast<unsigned>(a.n_imgs));
+  polar_fft_kernel<R><<<grid, 256, smem, st>>>(g, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
   if (a.n_imgs <= 0 || a.rows_per_img <= 0) return cudaSuccess;
   const size_t fixed = (static_cast<size_t>((g.L * g.L + 3) & ~3)) * sizeof(float) + g.M * sizeof(float2);
@@ -135,19 +197,15 @@ cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st)
   // two CTAs per SM when the rows fit in ~110 KB, else as many rows as fit in 200 KB
   int R = static_cast<int>((112640 > fixed ? 112640 - fixed : 0) / per_row);
   if (R < 1) R = static_cast<int>((204800 - fixed) / per_row);
-  R = R < 1 ? 1 : (R > 8 ? 8 : R);
+  R = R < 1 ? 1 : (R > 4 ? 4 : R);
   if (R > a.rows_per_img) R = a.rows_per_img;
   const size_t smem = fixed + per_row * R;
-  static size_t attr_set = 0;
-  if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(polar_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = smem;
+  switch (R) {
+    case 1: return launch_polar_r<1>(g, a, smem, st);
+    case 2: return launch_polar_r<2>(g, a, smem, st);
+    case 3: return launch_polar_r<3>(g, a, smem, st);
+    default: return launch_polar_r<4>(g, a, smem, st);
   }
-  dim3 grid((a.rows_per_img + R - 1) / R, static_cast<unsigned>(a.n_imgs));
-  polar_fft_kernel<<<grid, 256, smem, st>>>(g, a, R);
-  return cudaGetLastError();
 }
 
 }  // namespace mra

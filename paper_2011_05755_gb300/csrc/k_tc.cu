@@ -13,10 +13,12 @@
 // (p rows) for 8 rows x 4 references.  A tile of 8 rows x 8 references is
 // two such MMAs per k-step.  Operands are BF16 (or FP16), accumulation FP32.
 //
-// The per-pair angular state stays FP32 in shared memory, the inverse DFT
-// and row maxima are FP32, and the 8 rows (reference, shift, mirror) with
-// the largest maxima per image are recomputed from scratch in FP32 by the
-// rescore kernel, whose argmax is the answer.
+// For M = 256 (rings up to 40) the per-pair angular state is kept as BF16 in
+// shared memory and the inverse angular DFT runs on tensor cores too
+// (cc_tc256_kernel); for other M the state stays FP32 and the inverse DFT
+// runs in FP32 (cc_tc_kernel).  Either way the row maxima select the 8 rows
+// (reference, shift, mirror) per image that the rescore kernel recomputes
+// from scratch in FP32; its argmax is the answer.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -92,7 +94,8 @@ struct TcShape {
   static constexpr int RT = kTile, KT = KT_, PAIRS = RT * KT;
   static constexpr int NBLK = KT / 4;  // MMAs (N-blocks of 4 references) per k-step
   static constexpr int WARPS = 16, THREADS = 32 * WARPS;
-  static constexpr size_t STATE = static_cast<size_t>(PAIRS) * M * sizeof(float2);
+  static constexpr int P = IfftShape<M>::P;  // float2 per pair buffer
+  static constexpr size_t STATE = static_cast<size_t>(PAIRS) * P * sizeof(float2);
   static constexpr size_t TW = M * sizeof(float2);
   static constexpr size_t BARS = WARPS * sizeof(uint64_t);
   // A: ks_max k-steps x 512 B, then B: NBLK x ks_max x 256 B
@@ -102,9 +105,295 @@ struct TcShape {
   __host__ __device__ static size_t smem(int ks_max) { return STATE + TW + BARS + WARPS * stage_bytes(ks_max); }
 };
 
-// XOR swizzle matching the epilogue's store pattern (lane 4g + t -> row g, ref t or t + 4).
-template <int KT>
-__device__ __forceinline__ int tc_swz(int p) { return ((p % KT) & 3) + 4 * ((p / KT) & 3); }
+// XOR swizzle (below T) matching the epilogue's store pattern
+// (lane 4g + t -> row g, ref t or t + 4).
+template <int M, int KT>
+__device__ __forceinline__ int tc_swz(int p) {
+  return (((p % KT) & 3) + 4 * ((p / KT) & 3)) & (IfftShape<M>::T - 1);
+}
+
+// ---------------------------------------------------------------------------
+// M = 256: contraction and inverse angular DFT both on tensor cores.
+//
+// The angular spectrum of a pair is kept in shared memory as BF16 (Re, Im)
+// words, 1 KB per pair: BF16 has the FP32 exponent range, so no scaling is
+// needed, and its rounding (2^-9) is of the same order as that of the BF16
+// contraction operands; the FP32 rescore of the top rows restores full
+// accuracy.  Word position of Z(f) in a pair's buffer:
+//     f ^ sw ^ (((f >> 5) & 3) << 3),   sw = 4 (pair / 8) + (pair % 4),
+// which makes both the contraction's stores (32 lanes, 32 pairs, one f) and
+// the inverse DFT's fragment loads (one pair, lanes 4g + t4 reading
+// f = 8 nb + g + 16 a) bank-conflict free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int z256_fold(int f) { return f ^ (((f >> 5) & 3) << 3); }
+__device__ __forceinline__ int z256_swz(int pair) { return 4 * (pair >> 3) + (pair & 3); }
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Lane-invariant parts of the inverse DFT, computed once per kernel: the
+// folded positions of the 8 spectrum words a lane loads, and the 8 stage
+// twiddles it applies.
+struct TcLane {
+  int zoff[8];    // z256_fold(f) for f = 8 nb + g + 16 a, a in {2 t4, 2 t4 + 1, 2 t4 + 8, 2 t4 + 9}
+  float2 tw[8];   // w256^(t k) for fragment (nb, q)
+};
+
+__device__ __forceinline__ void tc_lane_init(TcLane &L, const float2 *tw, int lane) {
+  const int g = lane >> 2, t4 = lane & 3;
+  const int aa[4] = {2 * t4, 2 * t4 + 1, 2 * t4 + 8, 2 * t4 + 9};
+#pragma unroll
+  for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) L.zoff[nb * 4 + e] = z256_fold(8 * nb + g + 16 * aa[e]);
+#pragma unroll
+  for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = g + 8 * (q >> 1), t = 8 * nb + 2 * t4 + (q & 1);
+      L.tw[nb * 4 + q] = tw[k * 16 + t];
+    }
+}
+
+// Inverse angular DFT of one pair (M = 256 = 16 x 16) on tensor cores by one
+// warp: Y(k, t) = sum_a w16^(a k) Z(t + 16 a) as a 32 x 32 x 16 real GEMM
+// (A = the DFT matrix [[C, -S], [S, C]], B = Z), twiddle w256^(t k) in FP32,
+// then c(k + 16 j) = sum_t w16^(t j) Y'(k, t) as a 16 x 32 x 32 real GEMM
+// whose A fragments are exactly the stage-1 accumulators.  BF16 operands,
+// FP32 accumulation.  Returns the row maxima of the real (unmirrored) and
+// imaginary (mirrored) parts; `dbg` (or null) receives every value:
+// dbg[j] = Re c(j), dbg[M + (j + M/2) mod M] = Im c(j).
+__device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, const TcLane &L,
+                                                const uint32_t (&a1)[16], const uint32_t (&b2)[16], int lane,
+                                                float &vu, float &vm, float *dbg) {
+  const int g = lane >> 2, t4 = lane & 3;
+  uint32_t z[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) z[e] = zp[L.zoff[e] ^ sw];
+  // B fragments: [re/im k-step][t block]; word halves are (Re, Im) of one f
+  uint2 b1[2][2];
+#pragma unroll
+  for (int nb = 0; nb < 2; ++nb) {
+    b1[0][nb] = make_uint2(__byte_perm(z[4 * nb], z[4 * nb + 1], 0x5410), __byte_perm(z[4 * nb + 2], z[4 * nb + 3], 0x5410));
+    b1[1][nb] = make_uint2(__byte_perm(z[4 * nb], z[4 * nb + 1], 0x7632), __byte_perm(z[4 * nb + 2], z[4 * nb + 3], 0x7632));
+  }
+  float d1[2][2][4];  // [re/im of Y][t block][fragment]
+#pragma unroll
+  for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb) {
+      d1[mb][nb][0] = d1[mb][nb][1] = d1[mb][nb][2] = d1[mb][nb][3] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint4 af = make_uint4(a1[(mb * 2 + ks) * 4 + 0], a1[(mb * 2 + ks) * 4 + 1], a1[(mb * 2 + ks) * 4 + 2],
+                                    a1[(mb * 2 + ks) * 4 + 3]);
+        mma16816<false>(d1[mb][nb], af, b1[ks][nb]);
+      }
+    }
+  // twiddle w256^(t k): fragment q of block nb holds k = g + 8 (q >> 1), t = 8 nb + 2 t4 + (q & 1)
+  float yr[2][4], yi[2][4];
+#pragma unroll
+  for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 w = L.tw[nb * 4 + q];
+      const float r = d1[0][nb][q], im = d1[1][nb][q];
+      yr[nb][q] = fmaf(r, w.x, -im * w.y);
+      yi[nb][q] = fmaf(r, w.y, im * w.x);
+    }
+  uint4 a2[2];  // [re/im k-step]
+  a2[0] = make_uint4(pack_bf2(yr[0][0], yr[0][1]), pack_bf2(yr[0][2], yr[0][3]), pack_bf2(yr[1][0], yr[1][1]),
+                     pack_bf2(yr[1][2], yr[1][3]));
+  a2[1] = make_uint4(pack_bf2(yi[0][0], yi[0][1]), pack_bf2(yi[0][2], yi[0][3]), pack_bf2(yi[1][0], yi[1][1]),
+                     pack_bf2(yi[1][2], yi[1][3]));
+  float d2[4][4];  // [(re/im of c, j block)][fragment]
+#pragma unroll
+  for (int nb = 0; nb < 4; ++nb) {
+    d2[nb][0] = d2[nb][1] = d2[nb][2] = d2[nb][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+      mma16816<false>(d2[nb], a2[ks], make_uint2(b2[(ks * 4 + nb) * 2], b2[(ks * 4 + nb) * 2 + 1]));
+  }
+  float u = fmaxf(fmaxf(d2[0][0], d2[0][1]), fmaxf(d2[0][2], d2[0][3]));
+  float m = fmaxf(fmaxf(d2[2][0], d2[2][1]), fmaxf(d2[2][2], d2[2][3]));
+  u = fmaxf(u, fmaxf(fmaxf(d2[1][0], d2[1][1]), fmaxf(d2[1][2], d2[1][3])));
+  m = fmaxf(m, fmaxf(fmaxf(d2[3][0], d2[3][1]), fmaxf(d2[3][2], d2[3][3])));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    u = fmaxf(u, __shfl_xor_sync(0xffffffffu, u, off));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  }
+  vu = u;
+  vm = m;
+  if (dbg) {
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = g + 8 * (q >> 1), j = 8 * (nb & 1) + 2 * t4 + (q & 1);
+        const int ang = k + 16 * j;
+        if (nb < 2)
+          dbg[ang] = d2[nb][q];
+        else
+          dbg[256 + ((ang + 128) & 255)] = d2[nb][q];
+      }
+  }
+}
+
+// M = 256 kernel: one CTA per tile of 8 rows x 8 references (64 pairs),
+// 8 warps, two CTAs per SM.  Phase 1 streams the tile's A and B fragments in
+// chunks of whole frequencies (at most kTc256ChunkKs k-steps, 1 KB each)
+// through two shared-memory buffers with TMA bulk copies issued by thread 0,
+// one mbarrier per buffer; warp w contracts frequencies f0 + w, f0 + w + 8, ...
+// of each chunk (two MMAs per k-step, one per 4-reference block) and stores
+// Z(f), Z(M - f) of its 32 lanes' pairs as BF16 words.  Phase 2: warp w takes
+// reference w of the tile and its 8 rows, one tensor-core inverse DFT each,
+// and writes the two row maxima.  Every wait is bounded; the CTA agrees on a
+// failed wait at the per-chunk barrier, thread 0 records it, waits (bounded)
+// for the copies still in flight, and the CTA leaves.
+constexpr int kTc256Warps = 8;
+constexpr int kTc256Threads = 32 * kTc256Warps;
+constexpr size_t kTc256Stage = static_cast<size_t>(kTc256ChunkKs) * 1024;
+constexpr size_t kTc256Smem = 2 * kTc256Stage + 64 * 256 * sizeof(uint32_t) + 256 * sizeof(float2) +
+                              2 * sizeof(uint64_t) + 8 * sizeof(int2);
+
+template <bool FP16>
+__global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, TcArgs a) {
+  constexpr int M = 256, PAIRS = 64;
+  extern __shared__ float4 smem_f4[];
+  unsigned char *stage = reinterpret_cast<unsigned char *>(smem_f4);
+  uint32_t *Zw = reinterpret_cast<uint32_t *>(stage + 2 * kTc256Stage);  // [64 pairs][256 words]
+  float2 *tw = reinterpret_cast<float2 *>(Zw + PAIRS * M);
+  uint64_t *full = reinterpret_cast<uint64_t *>(tw + M);
+  int2 *rinfo = reinterpret_cast<int2 *>(full + 2);  // {image, shift} of the tile's rows
+
+  const int kt = blockIdx.x;
+  const int64_t rt = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nch = g.NCH;
+  for (int i = tid; i < M; i += kTc256Threads) tw[i] = g.inv_tw[i];
+  if (tid < 8) {
+    const int64_t row = rt * 8 + tid;
+    const int img = static_cast<int>(static_cast<uint32_t>(row) / static_cast<uint32_t>(g.S));  // rows < 2^31
+    rinfo[tid] = make_int2(img, static_cast<int>(row - static_cast<int64_t>(img) * g.S));
+  }
+  if (tid == 0) {
+    mbar_init(full, 1);
+    mbar_init(full + 1, 1);
+  }
+  mbar_init_fence();
+  __syncthreads();
+
+  auto issue = [&](int c) {  // thread 0: stage chunk c into buffer c & 1
+    const int k0 = g.kso[g.chunk_f[c]];
+    const uint32_t nks = static_cast<uint32_t>(g.kso[g.chunk_f[c + 1]] - k0);
+    unsigned char *dst = stage + (c & 1) * kTc256Stage;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(full + (c & 1), nks * 1024u);
+    bulk_g2s(dst, a.A16 + (rt * g.KS + k0) * 32, nks * 512u, full + (c & 1));
+    bulk_g2s(dst + nks * 512u, a.B16 + ((static_cast<int64_t>(kt) * 2) * g.KS + k0) * 32, nks * 256u, full + (c & 1));
+    bulk_g2s(dst + nks * 768u, a.B16 + ((static_cast<int64_t>(kt) * 2 + 1) * g.KS + k0) * 32, nks * 256u,
+             full + (c & 1));
+  };
+  if (tid == 0) {
+    issue(0);
+    if (nch > 1) issue(1);
+  }
+
+  // ---------------- Phase 1: tensor-core contraction ----------------
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int sw = 4 * g8 + t4;                 // z256_swz of both of this lane's pairs
+  uint32_t *z0 = Zw + (8 * g8 + t4) * M;      // pair (row g8, reference t4)
+  uint32_t *z1 = z0 + 4 * M;                  // pair (row g8, reference 4 + t4)
+  int c = 0;
+  bool failed = false;
+  for (; c < nch; ++c) {
+    const int buf = c & 1;
+    const bool ok = mbar_wait_bounded(full + buf, static_cast<uint32_t>((c >> 1) & 1),
+                                      c == 0 ? a.first_wait_limit : a.wait_limit);
+    if (ok) {
+      const int f0 = g.chunk_f[c], f1 = g.chunk_f[c + 1];
+      const int kbase = g.kso[f0];
+      const int nks_c = g.kso[f1] - kbase;
+      const uint4 *stA = reinterpret_cast<const uint4 *>(stage + buf * kTc256Stage);
+      const uint2 *stB0 = reinterpret_cast<const uint2 *>(stage + buf * kTc256Stage + static_cast<size_t>(nks_c) * 512);
+      const uint2 *stB1 = stB0 + nks_c * 32;
+      for (int f = f0 + warp; f < f1; f += kTc256Warps) {
+        const int j1 = g.kso[f + 1] - kbase;
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int j = g.kso[f] - kbase; j < j1; ++j) {
+          const uint4 af = stA[j * 32 + lane];
+          mma16816<FP16>(d0, af, stB0[j * 32 + lane]);
+          mma16816<FP16>(d1, af, stB1[j * 32 + lane]);
+        }
+        // lane (g8, t4): d[0..1] = Re/Im Z(f), d[2..3] = Im/Re Z(M - f)
+        const int pf = z256_fold(f) ^ sw;
+        z0[pf] = pack_bf2(d0[0], d0[1]);
+        z1[pf] = pack_bf2(d1[0], d1[1]);
+        if (f != 0 && f != M / 2) {
+          const int pm = z256_fold(M - f) ^ sw;
+          z0[pm] = pack_bf2(d0[3], d0[2]);
+          z1[pm] = pack_bf2(d1[3], d1[2]);
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {  // uniform: every thread leaves the loop
+      failed = true;
+      break;
+    }
+    if (tid == 0 && c + 2 < nch) issue(c + 2);
+  }
+  if (failed) {
+    if (tid == 0) {
+      atomicOr(a.err, 1);
+      // let the copies still in flight land before the CTA's memory goes
+      mbar_wait_bounded(full + (c & 1), static_cast<uint32_t>((c >> 1) & 1), a.wait_limit);
+      if (c + 1 < nch) mbar_wait_bounded(full + ((c + 1) & 1), static_cast<uint32_t>(((c + 1) >> 1) & 1), a.wait_limit);
+    }
+    return;
+  }
+
+  // ---------------- Phase 2: tensor-core inverse DFT, row maxima ----------------
+  uint32_t a1[16], b2[16];
+  {
+    const uint4 *fa = reinterpret_cast<const uint4 *>(g.dft16) + lane * 4;
+    const uint4 *fb = reinterpret_cast<const uint4 *>(g.dft16 + 512) + lane * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint4 va = __ldg(fa + i), vb = __ldg(fb + i);
+      a1[4 * i] = va.x;
+      a1[4 * i + 1] = va.y;
+      a1[4 * i + 2] = va.z;
+      a1[4 * i + 3] = va.w;
+      b2[4 * i] = vb.x;
+      b2[4 * i + 1] = vb.y;
+      b2[4 * i + 2] = vb.z;
+      b2[4 * i + 3] = vb.w;
+    }
+  }
+  TcLane Ln;
+  tc_lane_init(Ln, tw, lane);
+  const int ref = kt * 8 + warp;  // pairs warp + 8 i: reference `warp` of the tile, row i
+  const int S = g.S;
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) {
+    const int pc = 8 * i + warp;
+    const int64_t row = rt * 8 + i;
+    const bool valid = row < a.rows && ref < a.K;
+    const int64_t img = rinfo[i].x;
+    const int s = rinfo[i].y;
+    float *dbg = (a.dbg_cc && valid) ? a.dbg_cc + ((img * a.K + ref) * S + s) * 2 * M : nullptr;
+    float vu, vm;
+    pair_idft_tc256(Zw + pc * M, z256_swz(pc), Ln, a1, b2, lane, vu, vm, dbg);
+    if (valid && lane == 0) {
+      float *rm = a.rowmax + (img * a.K + ref) * static_cast<int64_t>(S) * 2 + 2 * s;
+      rm[0] = vu;
+      rm[1] = g.mirror ? vm : -INFINITY;
+    }
+  }
+}
 
 template <int M, int KT, bool FP16>
 __global__ void __launch_bounds__(TcShape<M, KT>::THREADS) cc_tc_kernel(Geometry g, TcArgs a) {
@@ -173,8 +462,8 @@ __global__ void __launch_bounds__(TcShape<M, KT>::THREADS) cc_tc_kernel(Geometry
 #pragma unroll
       for (int nb = 0; nb < Sh::NBLK; ++nb) {
         const int pa = g8 * KT + 4 * nb + t4;
-        float2 *za = Zs + pa * M;
-        const int sa = tc_swz<KT>(pa);
+        float2 *za = Zs + pa * Sh::P;
+        const int sa = tc_swz<M, KT>(pa);
         za[f ^ sa] = make_float2(d[nb][0], d[nb][1]);
         if (f != 0 && f != M / 2) za[(M - f) ^ sa] = make_float2(d[nb][3], d[nb][2]);
       }
@@ -194,9 +483,9 @@ __global__ void __launch_bounds__(TcShape<M, KT>::THREADS) cc_tc_kernel(Geometry
     const int64_t row = rt * Sh::RT + pc / KT;
     const int ref = kt * KT + pc % KT;
     const bool valid = in_tile && row < a.rows && ref < a.K;
-    float2 *zp = Zs + pc * M;
+    float2 *zp = Zs + pc * Sh::P;
     float2 y[IfftShape<M>::KK][T];
-    pair_ifft<M>(zp, tc_swz<KT>(pc), zp, t, in_tile, tw, y);
+    pair_ifft<M>(zp, tc_swz<M, KT>(pc), zp, t, in_tile, tw, y);
     float vu = -INFINITY, vm = -INFINITY;
 #pragma unroll
     for (int kk = 0; kk < U / T; ++kk)
@@ -305,7 +594,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
   float2 *twf = reinterpret_cast<float2 *>(im + LLp);
   float2 *twi = twf + M;
   float2 *Z = twi + M;
-  float2 *spec = Z + M;
+  float2 *spec = Z + IfftShape<M>::P;
   float *samp = reinterpret_cast<float *>(spec + ((g.NBIN + 1) & ~1));
   const float c0 = 0.5f * static_cast<float>(L);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -423,13 +712,30 @@ size_t cc_tc_smem(int M, int ks_max) {
     case 32: return TcShape<32, 8>::smem(ks_max);
     case 64: return TcShape<64, 8>::smem(ks_max);
     case 128: return TcShape<128, 8>::smem(ks_max);
-    case 256: return TcShape<256, 8>::smem(ks_max);
+    case 256: return kTc256Smem;
     case 512: return TcShape<512, 4>::smem(ks_max);
     default: return 0;
   }
 }
 
+template <bool FP16>
+static cudaError_t launch_tc256(const Geometry &g, const TcArgs &a, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(cc_tc256_kernel<FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kTc256Smem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t row_tiles = (a.rows + kTile - 1) / kTile;
+  if (row_tiles <= 0) return cudaSuccess;
+  dim3 grid((a.K + kTile - 1) / kTile, static_cast<unsigned>(row_tiles));
+  cc_tc256_kernel<FP16><<<grid, kTc256Threads, kTc256Smem, st>>>(g, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStream_t st) {
+  if (g.M == 256) return fp16 ? launch_tc256<true>(g, a, st) : launch_tc256<false>(g, a, st);
 #define MRA_TC_CASE(MM, KK) \
   case MM: return fp16 ? launch_tc_t<MM, KK, true>(g, a, st) : launch_tc_t<MM, KK, false>(g, a, st);
   switch (g.M) {
@@ -437,7 +743,6 @@ cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStre
     MRA_TC_CASE(32, 8)
     MRA_TC_CASE(64, 8)
     MRA_TC_CASE(128, 8)
-    MRA_TC_CASE(256, 8)
     MRA_TC_CASE(512, 4)
     default: return cudaErrorInvalidValue;
   }
@@ -451,7 +756,9 @@ cudaError_t launch_top8(const float *rowmax, int64_t n, int nrows, int *cand, cu
 }
 
 size_t rescore_smem(const Geometry &g) {
-  return static_cast<size_t>((g.L * g.L + 3) & ~3) * sizeof(float) + 3 * g.M * sizeof(float2) +
+  const int T = g.M >= 256 ? 16 : g.M / 16;
+  const int P = T * (g.M / T + 1);
+  return static_cast<size_t>((g.L * g.L + 3) & ~3) * sizeof(float) + (2 * g.M + P) * sizeof(float2) +
          static_cast<size_t>((g.NBIN + 1) & ~1) * sizeof(float2) + static_cast<size_t>(g.NS) * sizeof(float);
 }
 

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "mra_internal.h"
 
 namespace {
@@ -334,8 +336,63 @@ int build_tables(mra_handle *h) {
   if ((rc = upload(h, kso, &g.kso, "k-step offsets"))) return rc;
   if ((rc = upload(h, ksinfo, &g.ksinfo, "k-step table"))) return rc;
   if ((rc = upload(h, binpos16, &g.binpos16, "16-bit bin positions"))) return rc;
+  {
+    // whole frequencies per staging chunk of the M = 256 kernel, greedily
+    std::vector<int> chunk_f(1, 0);
+    for (int f = 0; f <= H; ++f) {
+      const int start = kso[chunk_f.back()];
+      if (f > chunk_f.back() && kso[f + 1] - start > mra::kTc256ChunkKs) chunk_f.push_back(f);
+    }
+    chunk_f.push_back(H + 1);
+    g.NCH = static_cast<int>(chunk_f.size()) - 1;
+    if ((rc = upload(h, chunk_f, &g.chunk_f, "staging chunks"))) return rc;
+  }
   h->half = c.precision != MRA_FP32;
   h->fp16 = c.precision == MRA_FP16_RESCORE;
+  // BF16 fragments of the 16-point DFT matrices for the tensor-core inverse DFT.
+  // Stage 1 (A, rows (re/im, k), cols (re/im, a)): [[C, -S], [S, C]];
+  // stage 2 (B, rows (re/im, t), cols (re/im, j)): [[C, S], [-S, C]];
+  // C = cos(2 pi x y / 16), S = sin(2 pi x y / 16).  Lane 4g + t4 of a warp.
+  {
+    std::vector<uint32_t> frag(1024);
+    auto h16 = [](double v) {  // BF16, round to nearest even (|v| <= 1)
+      const float x = static_cast<float>(v);
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      return (u + 0x7fffu + ((u >> 16) & 1u)) >> 16;
+    };
+    auto F = [](int blk_r, int blk_c, int x, int y, bool stage2) {
+      const double th = kTwoPi * x * y / 16.0;
+      const double C = std::cos(th), Sn = std::sin(th);
+      if (blk_r == blk_c) return C;
+      if (!stage2) return blk_r == 0 ? -Sn : Sn;   // stage 1: [[C,-S],[S,C]] (row block, col block)
+      return blk_r == 0 ? Sn : -Sn;                 // stage 2: [[C,S],[-S,C]] (K block, N block)
+    };
+    for (int lane = 0; lane < 32; ++lane) {
+      const int gg = lane >> 2, t4 = lane & 3;
+      // stage-1 A fragments: index (mb * 2 + ks) * 4 + reg
+      for (int mb = 0; mb < 2; ++mb)
+        for (int ks = 0; ks < 2; ++ks) {
+          const int rows[4] = {gg, gg + 8, gg, gg + 8};
+          const int cols[4] = {2 * t4, 2 * t4, 2 * t4 + 8, 2 * t4 + 8};
+          for (int r = 0; r < 4; ++r) {
+            const double lo = F(mb, ks, rows[r], cols[r], false), hi = F(mb, ks, rows[r], cols[r] + 1, false);
+            frag[lane * 16 + (mb * 2 + ks) * 4 + r] = h16(lo) | (h16(hi) << 16);
+          }
+        }
+      // stage-2 B fragments: index (ks * 4 + nb) * 2 + reg; column j = 8 (nb % 2) + gg, out block nb / 2
+      for (int ks = 0; ks < 2; ++ks)
+        for (int nb = 0; nb < 4; ++nb) {
+          const int j = 8 * (nb % 2) + gg, ob = nb / 2;
+          for (int r = 0; r < 2; ++r) {
+            const int t0 = 2 * t4 + 8 * r;
+            const double lo = F(ks, ob, t0, j, true), hi = F(ks, ob, t0 + 1, j, true);
+            frag[512 + lane * 16 + (ks * 4 + nb) * 2 + r] = h16(lo) | (h16(hi) << 16);
+          }
+        }
+    }
+    if ((rc = upload(h, frag, &g.dft16, "DFT fragments"))) return rc;
+  }
   if ((rc = dev_alloc(h, &h->d_err, sizeof(int), "failure flags"))) return rc;
   h->tables.push_back(h->d_err);
   cudaError_t e = cudaMemset(h->d_err, 0, sizeof(int));
@@ -357,6 +414,9 @@ int ensure_chunk_workspace(mra_handle *h) {
       if (chunk < 1) chunk = 1;
       if (chunk > 65536) chunk = 65536;
     }
+    // row tiles of one chunk index the contraction kernels' grid.y (<= 65535)
+    const int64_t max_chunk = (int64_t(65535) * mra::kTile) / S;
+    if (chunk > max_chunk) chunk = static_cast<int>(max_chunk < 1 ? 1 : max_chunk);
     h->chunk = chunk;
     const int64_t tiles = (int64_t(chunk) * S + mra::kTile - 1) / mra::kTile;
     int rc;
@@ -480,8 +540,9 @@ void free_all(mra_handle *h) {
 }
 
 // Polls of an mbarrier before a kernel gives up waiting for its own bulk
-// copies (each poll suspends for a hardware-chosen interval; ~1 s in total).
-constexpr uint32_t kWaitLimit = 1u << 20;
+// copies (each poll sleeps until the copies land or at most 0.5 ms; ~1 s in
+// total).
+constexpr uint32_t kWaitLimit = 2000;
 
 // Tests of the time-out path shorten each warp's first wait with
 // MRA_DEBUG_FIRST_WAIT_LIMIT (e.g. 0: give up at once, then drain normally).
@@ -684,6 +745,49 @@ int mra_set_refs(mra_t h, const float *d_refs, int32_t K, mra_stream_t stream) {
   return MRA_OK;
 }
 
+int mra_copy_refs(mra_t dst, mra_t src, mra_stream_t stream) {
+  if (int rc = need_handle(dst)) return rc;
+  if (!src) return set_err(dst, MRA_EINVAL, "source handle is NULL");
+  if (src == dst) return MRA_OK;
+  if (src->K == 0) return set_err(dst, MRA_ESTATE, "source handle holds no references");
+  const mra_config_t &a = dst->cfg, &b = src->cfg;
+  if (a.L != b.L || a.first_ring != b.first_ring || a.last_ring != b.last_ring || a.ring_step != b.ring_step ||
+      a.shift_range != b.shift_range || a.shift_step != b.shift_step || a.mirror != b.mirror ||
+      a.precision != b.precision)
+    return set_err(dst, MRA_EINVAL, "source and destination configurations differ (chunk_images may differ)");
+  if (src->device != dst->device) return set_err(dst, MRA_EINVAL, "source handle lives on another device");
+  if (int rc = select_device(dst)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int Kpad = src->Kpad;
+  if (Kpad != dst->Kpad) {
+    dev_free(dst, dst->B, static_cast<size_t>(dst->Kpad) * dst->NB * sizeof(float2));
+    dst->B = nullptr;
+    dst->Kpad = 0;
+    dst->K = 0;
+    if (int rc = dev_alloc(dst, &dst->B, static_cast<size_t>(Kpad) * dst->NB * sizeof(float2), "reference spectra"))
+      return rc;
+    dst->Kpad = Kpad;
+  }
+  dst->K = 0;
+  cudaError_t e = cudaMemcpyAsync(dst->B, src->B, static_cast<size_t>(Kpad) * dst->NB * sizeof(float2),
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_err(dst, e, "cudaMemcpyAsync(reference spectra)");
+  if (dst->half) {
+    const size_t b16 = static_cast<size_t>(Kpad / mra::kTile) * 2 * dst->g.KS * 32 * sizeof(uint2);
+    if (!dst->B16 || Kpad > dst->B16_refs) {
+      dev_free(dst, dst->B16, static_cast<size_t>(dst->B16_refs / mra::kTile) * 2 * dst->g.KS * 32 * sizeof(uint2));
+      dst->B16 = nullptr;
+      dst->B16_refs = 0;
+      if (int rc = dev_alloc(dst, &dst->B16, b16, "reference fragments")) return rc;
+      dst->B16_refs = Kpad;
+    }
+    e = cudaMemcpyAsync(dst->B16, src->B16, b16, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_err(dst, e, "cudaMemcpyAsync(reference fragments)");
+  }
+  dst->K = src->K;
+  return MRA_OK;
+}
+
 int mra_align(mra_t h, const float *d_imgs, int64_t n, mra_pose_t *d_poses, mra_stream_t stream) {
   if (int rc = need_handle(h)) return rc;
   if (n < 0) return set_err(h, MRA_EINVAL, "n must be >= 0");
@@ -758,6 +862,20 @@ int mra_average(mra_t h, const float *d_imgs, const mra_pose_t *d_poses, int64_t
     rc = check_launch(h, mra::launch_average_finalize(h->g, h->K, h->avg_sum, h->avg_comp, d_counts, d_avg, st),
                       "average finalize kernel");
   prof_end(h, rec, mra::kClassSumLaunches + 1, st);
+  return rc;
+}
+
+int mra_refresh_refs(mra_t h, float *d_refs, const int32_t *d_counts, int32_t K, const int32_t *d_reseed,
+                     const float *d_imgs, int64_t n, mra_stream_t stream) {
+  if (int rc = need_handle(h)) return rc;
+  if (K < 1 || !d_refs || !d_counts) return set_err(h, MRA_EINVAL, "need K >= 1, d_refs and d_counts");
+  if (d_reseed && (!d_imgs || n < 1)) return set_err(h, MRA_EINVAL, "reseeding needs d_imgs and n >= 1");
+  if (int rc = select_device(h)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int rec = prof_begin(h, MRA_STAGE_AVERAGE, st);
+  const int rc = check_launch(h, mra::launch_refresh_refs(h->cfg.L, d_refs, d_counts, K, d_reseed, d_imgs, n, st),
+                              "reference refresh kernel");
+  prof_end(h, rec, 1, st);
   return rc;
 }
 

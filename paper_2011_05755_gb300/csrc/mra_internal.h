@@ -37,7 +37,17 @@ struct Geometry {
   const int *kso;         // [M/2 + 2]
   const int2 *ksinfo;     // [KS]
   const int *binpos16;    // [NBIN] position kso[f] * 16 + (ring - first ring of f)
+  // BF16 mma fragments of the two 16-point DFT stages of the tensor-core
+  // inverse angular DFT (M = 256): [0, 512) stage-1 A, [512, 1024) stage-2 B,
+  // each [32 lanes][16 words].
+  const uint32_t *dft16;
+  // Staging chunks of the M = 256 tensor-core kernel: chunk c holds the whole
+  // frequencies [chunk_f[c], chunk_f[c + 1]), at most kTc256ChunkKs k-steps.
+  int NCH;
+  const int *chunk_f;     // [NCH + 1]
 };
+
+constexpr int kTc256ChunkKs = 20;
 
 struct PolarArgs {
   const float *imgs;   // [n][L][L]
@@ -124,6 +134,8 @@ constexpr int kAvgChunk = 64;    // images per partial-sum chunk
 cudaError_t launch_class_sums(const Geometry &g, const float *imgs, const void *poses, int64_t n,
                               int K, const AvgWork &w, float *sum, float *comp, int *counts,
                               bool accumulate, cudaStream_t st);
+cudaError_t launch_refresh_refs(int L, float *refs, const int *counts, int K, const int *reseed, const float *imgs,
+                                int64_t n, cudaStream_t st);
 cudaError_t launch_average_finalize(const Geometry &g, int K, const float *sum, const float *comp,
                                     const int *counts, float *avg, cudaStream_t st);
 

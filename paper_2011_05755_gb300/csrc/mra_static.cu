@@ -291,8 +291,8 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
     ca.best = d_best;
     ca.seg_max = seg_max;
     ca.err = d_err;
-    ca.wait_limit = 1u << 20;
-    ca.first_wait_limit = 1u << 20;
+    ca.wait_limit = 2000;  // ~1 s of 0.5 ms polls
+    ca.first_wait_limit = 2000;
     if ((e = mra::launch_cc_fp32(g, ca, st)) != cudaSuccess)
       return fail(MRA_ECUDA, "contraction kernel: %s", cudaGetErrorString(e));
     if ((e = mra::launch_decode(g, d_best, cnt, K, d_poses + c0, st)) != cudaSuccess)

@@ -79,6 +79,64 @@ __device__ __forceinline__ void warp_fft_inplace(float2 *z, int H, int logH, int
   }
 }
 
+// Forward FFT of H complex points (power of two, 4..256) held in shared
+// memory, by a group of T threads of one warp (T = H / 16 for H >= 32, else
+// one thread): thread t transforms z(t + T a), a = 0..U-1, in registers,
+// multiplies by exp(-2 pi i t k / H), the group transposes in place (XOR
+// swizzle), finishes the length-T transforms, and writes X(k + U jj) back in
+// natural order.  Every lane of the warp must call it (it uses __syncwarp);
+// lanes with `active` false do no stores.  fwd_tw[q] = exp(-2 pi i q / M).
+template <int H>
+struct GroupFft {
+  static constexpr int T = H >= 32 ? H / 16 : 1;
+  static constexpr int U = H / T;
+  static constexpr int KK = U / T;
+};
+
+template <int H>
+__device__ __forceinline__ void group_fft(float2 *z, int t, bool active, const float2 *fwd_tw, int M) {
+  constexpr int T = GroupFft<H>::T;
+  constexpr int U = GroupFft<H>::U;
+  float2 x[U];
+#pragma unroll
+  for (int a = 0; a < U; ++a) x[a] = z[t + T * a];
+  reg_fft<U, -1>(x);
+  if constexpr (T == 1) {
+    __syncwarp();
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < U; ++k) z[k] = x[k];
+    }
+    __syncwarp();
+  } else {
+    const int tstep = (M / H) * t;
+#pragma unroll
+    for (int k = 1; k < U; ++k) x[k] = cmul(x[k], fwd_tw[(tstep * k) & (M - 1)]);
+    __syncwarp();
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < U; ++k) z[k * T + (t ^ (k & (T - 1)))] = x[k];
+    }
+    __syncwarp();
+    float2 y[GroupFft<H>::KK][T];
+#pragma unroll
+    for (int kk = 0; kk < GroupFft<H>::KK; ++kk) {
+      const int k = t + T * kk;
+#pragma unroll
+      for (int tt = 0; tt < T; ++tt) y[kk][tt] = z[k * T + (tt ^ t)];
+      reg_fft<T, -1>(y[kk]);
+    }
+    __syncwarp();
+    if (active) {
+#pragma unroll
+      for (int kk = 0; kk < GroupFft<H>::KK; ++kk)
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) z[t + T * kk + U * jj] = y[kk][jj];
+    }
+    __syncwarp();
+  }
+}
+
 // Bin k (0..H) of the real DFT of the N = 2H samples packed as
 // z_q = x_{2q} + i x_{2q+1} and transformed by warp_fft_inplace:
 // X(k) = E(k) + exp(-2 pi i k / N) O(k).

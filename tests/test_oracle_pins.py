@@ -375,3 +375,53 @@ def test_cc_table_consistent_with_cc_rings():
             for m in (0, 1):
                 xk = O.polar_samples(img, rings, sx, sy, m)
                 np.testing.assert_allclose(c[k, si, m], O.cc_rings(xk, yk, rings, 2), atol=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# Classification loop: normalisation and the fixed point of one pass
+# ----------------------------------------------------------------------------
+
+def test_normalize_invariants():
+    x = RNG.standard_normal((20, 20)) * 3.0 + 2.0
+    z = O.normalize(x)
+    assert abs(z.mean()) < 1e-12
+    assert math.sqrt(np.mean(z * z)) == pytest.approx(1.0, abs=1e-12)
+    np.testing.assert_allclose(O.normalize(5.0 * x - 7.0), z, atol=1e-12)   # affine invariance (a > 0)
+    np.testing.assert_allclose(O.normalize(-x), -z, atol=1e-12)             # odd under negation
+    assert np.array_equal(O.normalize(np.full((6, 6), 4.5)), np.zeros((6, 6)))
+    # library routine in a special case: population standard deviation
+    np.testing.assert_allclose(z, (x - x.mean()) / np.std(x, ddof=0), atol=1e-12)
+
+
+def test_refresh_rules():
+    refs = RNG.standard_normal((3, 8, 8))
+    avg = RNG.standard_normal((3, 8, 8)) + 1.0
+    imgs = RNG.standard_normal((4, 8, 8))
+    out = O.refresh_refs(refs, avg, np.array([2, 0, 0]), np.array([-1, 3, -1]), imgs)
+    np.testing.assert_allclose(out[0], O.normalize(avg[0]))
+    np.testing.assert_allclose(out[1], O.normalize(imgs[3]))
+    assert np.array_equal(out[2], refs[2])
+
+
+def test_classification_pass_fixed_point():
+    """Particles that are exact grid permutations of compact references: one
+    pass assigns every particle to its source class and returns the
+    normalised references (the aligned particles are the references pixel for
+    pixel, so every class average is its reference).  The references are
+    scaled to equal ring-weighted energy E: by Cauchy-Schwarz on the ring
+    spectra (Parseval with the split Nyquist term) any other class scores at
+    most E, which the source class reaches exactly."""
+    L = 32
+    refs = _compact_refs(3, L, seed=17)
+    rings = O.ring_table(1, 8, 1)
+    for k in range(3):
+        xs = O.polar_samples(refs[k], rings)
+        refs[k] /= math.sqrt(O.cc_rings(xs, xs, rings, 1)[0])
+    cfg = O.MRAConfig(L, 1, 8, 1, 1.0, 1.0, 1)
+    cases = [(0, 1, 1, 0, 0), (1, 3, 0, -1, 1), (2, 2, -1, 1, 1), (1, 0, 1, 0, 0), (2, 1, 0, 0, 0)]
+    imgs = np.stack([_permute(refs[k], q, tx, ty, m) for k, q, tx, ty, m in cases])
+    poses, new_refs, counts = O.classify_iteration(imgs, refs, cfg)
+    assert [p.k for p in poses] == [c[0] for c in cases]
+    assert list(counts) == [1, 2, 2]
+    want = (refs - refs.mean(axis=(1, 2), keepdims=True)) / refs.std(axis=(1, 2), keepdims=True)
+    np.testing.assert_allclose(new_refs, want, atol=1e-9)
