@@ -22,6 +22,11 @@
 
 namespace mra {
 
+// Row stride of the sample buffer: >= NS and 16 floats off a multiple of 32,
+// so the ring-FFT jobs of consecutive rows start in opposite halves of the
+// shared-memory banks.
+__host__ __device__ inline int sample_stride(int NS) { return NS + ((16 - NS) & 31); }
+
 // All (ring, row) jobs of one ring-length class [i0, i1) of a CTA: forward
 // FFT of the packed samples, real split, weights, and the spectrum written in
 // the layout the path needs (FP32 tiled, 16-bit q/p planes, debug).
@@ -42,7 +47,7 @@ __device__ __forceinline__ int ring_class(const Geometry &g, const PolarArgs &a,
     const int ring = i0 + jc / nrows;
     const int i = jc % nrows;
     const int4 rd = g.rings[ring];  // {N, sample offset, natural-bin offset, log2(N/2)}
-    float2 *z = reinterpret_cast<float2 *>(smem + i * g.NS + rd.y);
+    float2 *z = reinterpret_cast<float2 *>(smem + i * sample_stride(g.NS) + rd.y);
     group_fft<H>(z, t, active, tws, g.M);
     if (active) {
       const int wstep = g.M / (2 * H);
@@ -72,58 +77,114 @@ __device__ __forceinline__ int ring_class(const Geometry &g, const PolarArgs &a,
   return (first_warp + (njobs + JPW - 1) / JPW) % nwarps;  // first warp of the next class
 }
 
-template <int R>
-__global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a) {
+// Shared-memory image floats: the image, or (TAPS) the image inside a zero
+// border of g.pad pixels.
+__host__ __device__ inline int image_floats(const Geometry &g, bool taps) {
+  const int Lp = taps ? g.L + 2 * g.pad : g.L;
+  return (Lp * Lp + 3) & ~3;
+}
+
+template <int R, bool TAPS>
+__global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs a) {
   extern __shared__ float4 smem_f4[];
   const int L = g.L, NS = g.NS, M = g.M;
+  const int NSp = sample_stride(NS);
   const int LL = L * L;
-  const int LLp = (LL + 3) & ~3;
   const int64_t img = blockIdx.y;
   const int s0 = blockIdx.x * R;                       // first shift of this CTA
   const int nrows = min(R, a.rows_per_img - s0);
   const int64_t row0 = img * a.rows_per_img + s0;
-  float *im = reinterpret_cast<float *>(smem_f4);       // [LLp] the image
-  float2 *tws = reinterpret_cast<float2 *>(im + LLp);    // [M] forward twiddles
-  float *smem = reinterpret_cast<float *>(tws + M);      // [R][NS] samples, then ring FFTs
+  float *im = reinterpret_cast<float *>(smem_f4);       // the image (with its zero border if TAPS)
+  float2 *tws = reinterpret_cast<float2 *>(im + image_floats(g, TAPS));  // [M] forward twiddles
+  float *smem = reinterpret_cast<float *>(tws + M);      // [R][NSp] samples, then ring FFTs
   const float c0 = 0.5f * static_cast<float>(L);
   // 16-bit paths: q / p planes [row][2][NB16] after the samples (zero = padding)
   const int NB16 = g.KS * 16;
-  unsigned short *planes = reinterpret_cast<unsigned short *>(smem + R * NS);
+  unsigned short *planes = reinterpret_cast<unsigned short *>(smem + R * NSp);
   if (a.out16)
     for (int idx = threadIdx.x; idx < R * NB16; idx += blockDim.x)
       reinterpret_cast<uint32_t *>(planes)[idx] = 0u;
-  {
-    const float *src = a.imgs + img * LL;
-    if ((LL & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+  const float *src = a.imgs + img * LL;
+  const bool vec = (L & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+  if constexpr (TAPS) {
+    // zero the bordered buffer, then copy the interior (pad is a multiple of 4)
+    const int Lp = L + 2 * g.pad;
+    for (int i = threadIdx.x; i < image_floats(g, true) / 4; i += blockDim.x)
+      reinterpret_cast<float4 *>(im)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    float *dst = im + g.pad * Lp + g.pad;
+    if (vec) {
+      const int W = L / 4;
+      for (int i = threadIdx.x; i < L * W; i += blockDim.x) {
+        const int y = i / W, x4 = i - y * W;
+        reinterpret_cast<float4 *>(dst + y * Lp)[x4] = __ldg(reinterpret_cast<const float4 *>(src + y * L) + x4);
+      }
+    } else {
+      for (int i = threadIdx.x; i < LL; i += blockDim.x) {
+        const int y = i / L, x = i - y * L;
+        dst[y * Lp + x] = __ldg(src + i);
+      }
+    }
+  } else {
+    if (vec) {
       const float4 *s4 = reinterpret_cast<const float4 *>(src);
       for (int i = threadIdx.x; i < LL / 4; i += blockDim.x) reinterpret_cast<float4 *>(im)[i] = __ldg(s4 + i);
     } else {
       for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(src + i);
     }
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = g.fwd_tw[i];
   }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = g.fwd_tw[i];
   __syncthreads();
 
   // Phase 1: samples x_r(theta_q) = I(c0 + s + r (cos theta_q, sin theta_q)).
-  float cx[R], cy[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    cx[i] = c0;
-    cy[i] = c0;
-    if (a.use_shifts && i < nrows) {
-      const float2 sh = g.shifts[s0 + i];
-      cx[i] += sh.x;
-      cy[i] += sh.y;
-    }
-  }
-  for (int q = threadIdx.x; q < NS; q += blockDim.x) {
-    const float2 o = g.offs[q];
+  if constexpr (TAPS) {
+    // integer shifts: the bilinear weights of a sample do not depend on the
+    // shift, which only moves the neighbourhood inside the bordered image
+    const int Lp = L + 2 * g.pad;
+    int soff[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-      if (i < nrows) {
-        const float v = bilinear_smem(im, L, cx[i] + o.x, cy[i] + o.y);
-        smem[i * NS + q] = v;
-        if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+      soff[i] = 0;
+      if (a.use_shifts && i < nrows) {
+        const float2 sh = g.shifts[s0 + i];
+        soff[i] = static_cast<int>(sh.y) * Lp + static_cast<int>(sh.x);
+      }
+    }
+    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
+      const float4 tp = __ldg(g.taps + q);
+      const int base = __float_as_int(tp.x);
+      const float fx = tp.y, fy = tp.z, gx = 1.f - fx, gy = 1.f - fy;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        if (i < nrows) {
+          const float *p = im + base + soff[i];
+          const float v = gy * (gx * p[0] + fx * p[1]) + fy * (gx * p[Lp] + fx * p[Lp + 1]);
+          smem[i * NSp + q] = v;
+          if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+        }
+      }
+    }
+  } else {
+    float cx[R], cy[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      cx[i] = c0;
+      cy[i] = c0;
+      if (a.use_shifts && i < nrows) {
+        const float2 sh = g.shifts[s0 + i];
+        cx[i] += sh.x;
+        cy[i] += sh.y;
+      }
+    }
+    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
+      const float2 o = g.offs[q];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        if (i < nrows) {
+          const float v = bilinear_smem(im, L, cx[i] + o.x, cy[i] + o.y);
+          smem[i * NSp + q] = v;
+          if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+        }
       }
     }
   }
@@ -175,24 +236,24 @@ __global__ void __launch_bounds__(256) polar_fft_kernel(Geometry g, PolarArgs a)
   }
 }
 
-template <int R>
+template <int R, bool TAPS>
 static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t smem, cudaStream_t st) {
   static size_t attr_set = 0;
   if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(polar_fft_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(polar_fft_kernel<R, TAPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
   dim3 grid((a.rows_per_img + R - 1) / R, static_cast<unsigned>(a.n_imgs));
-  polar_fft_kernel<R><<<grid, 256, smem, st>>>(g, a);
+  polar_fft_kernel<R, TAPS><<<grid, 256, smem, st>>>(g, a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
-  if (a.n_imgs <= 0 || a.rows_per_img <= 0) return cudaSuccess;
-  const size_t fixed = (static_cast<size_t>((g.L * g.L + 3) & ~3)) * sizeof(float) + g.M * sizeof(float2);
-  size_t per_row = static_cast<size_t>(g.NS) * sizeof(float);
+template <bool TAPS>
+static cudaError_t launch_polar_t(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
+  const size_t fixed = static_cast<size_t>(image_floats(g, TAPS)) * sizeof(float) + g.M * sizeof(float2);
+  size_t per_row = static_cast<size_t>(sample_stride(g.NS)) * sizeof(float);
   if (a.out16) per_row += static_cast<size_t>(g.KS) * 16 * 2 * sizeof(unsigned short);
   // two CTAs per SM when the rows fit in ~110 KB, else as many rows as fit in 200 KB
   int R = static_cast<int>((112640 > fixed ? 112640 - fixed : 0) / per_row);
@@ -201,11 +262,16 @@ cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st)
   if (R > a.rows_per_img) R = a.rows_per_img;
   const size_t smem = fixed + per_row * R;
   switch (R) {
-    case 1: return launch_polar_r<1>(g, a, smem, st);
-    case 2: return launch_polar_r<2>(g, a, smem, st);
-    case 3: return launch_polar_r<3>(g, a, smem, st);
-    default: return launch_polar_r<4>(g, a, smem, st);
+    case 1: return launch_polar_r<1, TAPS>(g, a, smem, st);
+    case 2: return launch_polar_r<2, TAPS>(g, a, smem, st);
+    case 3: return launch_polar_r<3, TAPS>(g, a, smem, st);
+    default: return launch_polar_r<4, TAPS>(g, a, smem, st);
   }
+}
+
+cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
+  if (a.n_imgs <= 0 || a.rows_per_img <= 0) return cudaSuccess;
+  return g.taps ? launch_polar_t<true>(g, a, st) : launch_polar_t<false>(g, a, st);
 }
 
 }  // namespace mra

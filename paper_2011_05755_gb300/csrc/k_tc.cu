@@ -162,9 +162,10 @@ __device__ __forceinline__ void tc_lane_init(TcLane &L, const float2 *tw, int la
 // (A = the DFT matrix [[C, -S], [S, C]], B = Z), twiddle w256^(t k) in FP32,
 // then c(k + 16 j) = sum_t w16^(t j) Y'(k, t) as a 16 x 32 x 32 real GEMM
 // whose A fragments are exactly the stage-1 accumulators.  BF16 operands,
-// FP32 accumulation.  Returns the row maxima of the real (unmirrored) and
-// imaginary (mirrored) parts; `dbg` (or null) receives every value:
-// dbg[j] = Re c(j), dbg[M + (j + M/2) mod M] = Im c(j).
+// FP32 accumulation.  Returns this lane's maxima of the real (unmirrored)
+// and imaginary (mirrored) parts (the caller reduces over the warp); `dbg`
+// (or null) receives every value: dbg[j] = Re c(j),
+// dbg[M + (j + M/2) mod M] = Im c(j).
 __device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, const TcLane &L,
                                                 const uint32_t (&a1)[16], const uint32_t (&b2)[16], int lane,
                                                 float &vu, float &vm, float *dbg) {
@@ -216,17 +217,10 @@ __device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, cons
     for (int ks = 0; ks < 2; ++ks)
       mma16816<false>(d2[nb], a2[ks], make_uint2(b2[(ks * 4 + nb) * 2], b2[(ks * 4 + nb) * 2 + 1]));
   }
-  float u = fmaxf(fmaxf(d2[0][0], d2[0][1]), fmaxf(d2[0][2], d2[0][3]));
-  float m = fmaxf(fmaxf(d2[2][0], d2[2][1]), fmaxf(d2[2][2], d2[2][3]));
-  u = fmaxf(u, fmaxf(fmaxf(d2[1][0], d2[1][1]), fmaxf(d2[1][2], d2[1][3])));
-  m = fmaxf(m, fmaxf(fmaxf(d2[3][0], d2[3][1]), fmaxf(d2[3][2], d2[3][3])));
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    u = fmaxf(u, __shfl_xor_sync(0xffffffffu, u, off));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-  }
-  vu = u;
-  vm = m;
+  vu = fmaxf(fmaxf(fmaxf(d2[0][0], d2[0][1]), fmaxf(d2[0][2], d2[0][3])),
+             fmaxf(fmaxf(d2[1][0], d2[1][1]), fmaxf(d2[1][2], d2[1][3])));
+  vm = fmaxf(fmaxf(fmaxf(d2[2][0], d2[2][1]), fmaxf(d2[2][2], d2[2][3])),
+             fmaxf(fmaxf(d2[3][0], d2[3][1]), fmaxf(d2[3][2], d2[3][3])));
   if (dbg) {
 #pragma unroll
     for (int nb = 0; nb < 4; ++nb)
@@ -242,38 +236,57 @@ __device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, cons
   }
 }
 
-// M = 256 kernel: one CTA per tile of 8 rows x 8 references (64 pairs),
-// 8 warps, two CTAs per SM.  Phase 1 streams the tile's A and B fragments in
-// chunks of whole frequencies (at most kTc256ChunkKs k-steps, 1 KB each)
-// through two shared-memory buffers with TMA bulk copies issued by thread 0,
-// one mbarrier per buffer; warp w contracts frequencies f0 + w, f0 + w + 8, ...
-// of each chunk (two MMAs per k-step, one per 4-reference block) and stores
-// Z(f), Z(M - f) of its 32 lanes' pairs as BF16 words.  Phase 2: warp w takes
-// reference w of the tile and its 8 rows, one tensor-core inverse DFT each,
-// and writes the two row maxima.  Every wait is bounded; the CTA agrees on a
-// failed wait at the per-chunk barrier, thread 0 records it, waits (bounded)
-// for the copies still in flight, and the CTA leaves.
+// Maxima over the 32 lanes of two values per lane in 5 shuffles: at the
+// first butterfly step lanes 0-15 keep `u` and lanes 16-31 keep `m`, so
+// afterwards lanes 0-15 hold max(u) and lanes 16-31 max(m).
+__device__ __forceinline__ float warp_max2(float u, float m, int lane) {
+  const bool hi = (lane & 16) != 0;
+  float v = fmaxf(hi ? m : u, __shfl_xor_sync(0xffffffffu, hi ? u : m, 16));
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// M = 256 kernel: one CTA per tile of 8 rows, looping over the reference
+// tiles of 8 (64 pairs each), 8 warps, two CTAs per SM.  Phase 1 streams a
+// tile's A and B fragments in chunks of whole frequencies (at most
+// kTc256ChunkKs k-steps, 1 KB each) through two shared-memory buffers with
+// TMA bulk copies issued by thread 0, one mbarrier per buffer; the copy of
+// chunk q + 2 (of this tile or the first two of the next one) starts as soon
+// as chunk q has been consumed, so the next tile's first chunks load while
+// this tile's inverse DFTs run.  Warp w contracts frequencies f0 + w,
+// f0 + w + 8, ... of each chunk (two MMAs per k-step, one per 4-reference
+// block) and stores Z(f), Z(M - f) of its 32 lanes' pairs as BF16 words.
+// Phase 2: warp w takes reference w of the tile and its 8 rows, one
+// tensor-core inverse DFT and one warp reduction of the two row maxima each.  Every wait is bounded; the CTA agrees on a failed wait at the
+// per-chunk barrier, thread 0 records it, waits (bounded) for the copies
+// still in flight, and the CTA leaves.
 constexpr int kTc256Warps = 8;
 constexpr int kTc256Threads = 32 * kTc256Warps;
+constexpr int kTc256MaxChunks = 32;
 constexpr size_t kTc256Stage = static_cast<size_t>(kTc256ChunkKs) * 1024;
 constexpr size_t kTc256Smem = 2 * kTc256Stage + 64 * 256 * sizeof(uint32_t) + 256 * sizeof(float2) +
-                              2 * sizeof(uint64_t) + 8 * sizeof(int2);
+                              2 * sizeof(uint64_t) + 8 * sizeof(int2) + (130 + kTc256MaxChunks + 2) * sizeof(int);
 
 template <bool FP16>
-__global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, TcArgs a) {
-  constexpr int M = 256, PAIRS = 64;
+__global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, TcArgs a, int ref_tiles) {
+  constexpr int M = 256, PAIRS = 64, NF = M / 2 + 1;
   extern __shared__ float4 smem_f4[];
   unsigned char *stage = reinterpret_cast<unsigned char *>(smem_f4);
   uint32_t *Zw = reinterpret_cast<uint32_t *>(stage + 2 * kTc256Stage);  // [64 pairs][256 words]
   float2 *tw = reinterpret_cast<float2 *>(Zw + PAIRS * M);
   uint64_t *full = reinterpret_cast<uint64_t *>(tw + M);
   int2 *rinfo = reinterpret_cast<int2 *>(full + 2);  // {image, shift} of the tile's rows
+  int *s_kso = reinterpret_cast<int *>(rinfo + 8);   // [NF + 1]
+  int *s_cf = s_kso + NF + 1;                        // [NCH + 1]
 
-  const int kt = blockIdx.x;
-  const int64_t rt = blockIdx.y;
+  const int64_t rt = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nch = g.NCH;
+  const int total = ref_tiles * nch;  // chunks over the whole reference loop
   for (int i = tid; i < M; i += kTc256Threads) tw[i] = g.inv_tw[i];
+  for (int i = tid; i <= NF; i += kTc256Threads) s_kso[i] = g.kso[i];
+  for (int i = tid; i <= nch; i += kTc256Threads) s_cf[i] = g.chunk_f[i];
   if (tid < 8) {
     const int64_t row = rt * 8 + tid;
     const int img = static_cast<int>(static_cast<uint32_t>(row) / static_cast<uint32_t>(g.S));  // rows < 2^31
@@ -286,76 +299,24 @@ __global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, 
   mbar_init_fence();
   __syncthreads();
 
-  auto issue = [&](int c) {  // thread 0: stage chunk c into buffer c & 1
-    const int k0 = g.kso[g.chunk_f[c]];
-    const uint32_t nks = static_cast<uint32_t>(g.kso[g.chunk_f[c + 1]] - k0);
-    unsigned char *dst = stage + (c & 1) * kTc256Stage;
+  auto issue = [&](int q) {  // thread 0: stage chunk q % nch of reference tile q / nch into buffer q & 1
+    const int kt = q / nch, c = q - kt * nch;
+    const int k0 = s_kso[s_cf[c]];
+    const uint32_t nks = static_cast<uint32_t>(s_kso[s_cf[c + 1]] - k0);
+    unsigned char *dst = stage + (q & 1) * kTc256Stage;
     fence_proxy_async();
-    mbar_arrive_expect_tx(full + (c & 1), nks * 1024u);
-    bulk_g2s(dst, a.A16 + (rt * g.KS + k0) * 32, nks * 512u, full + (c & 1));
-    bulk_g2s(dst + nks * 512u, a.B16 + ((static_cast<int64_t>(kt) * 2) * g.KS + k0) * 32, nks * 256u, full + (c & 1));
+    mbar_arrive_expect_tx(full + (q & 1), nks * 1024u);
+    bulk_g2s(dst, a.A16 + (rt * g.KS + k0) * 32, nks * 512u, full + (q & 1));
+    bulk_g2s(dst + nks * 512u, a.B16 + ((static_cast<int64_t>(kt) * 2) * g.KS + k0) * 32, nks * 256u, full + (q & 1));
     bulk_g2s(dst + nks * 768u, a.B16 + ((static_cast<int64_t>(kt) * 2 + 1) * g.KS + k0) * 32, nks * 256u,
-             full + (c & 1));
+             full + (q & 1));
   };
   if (tid == 0) {
     issue(0);
-    if (nch > 1) issue(1);
+    if (total > 1) issue(1);
   }
 
-  // ---------------- Phase 1: tensor-core contraction ----------------
-  const int g8 = lane >> 2, t4 = lane & 3;
-  const int sw = 4 * g8 + t4;                 // z256_swz of both of this lane's pairs
-  uint32_t *z0 = Zw + (8 * g8 + t4) * M;      // pair (row g8, reference t4)
-  uint32_t *z1 = z0 + 4 * M;                  // pair (row g8, reference 4 + t4)
-  int c = 0;
-  bool failed = false;
-  for (; c < nch; ++c) {
-    const int buf = c & 1;
-    const bool ok = mbar_wait_bounded(full + buf, static_cast<uint32_t>((c >> 1) & 1),
-                                      c == 0 ? a.first_wait_limit : a.wait_limit);
-    if (ok) {
-      const int f0 = g.chunk_f[c], f1 = g.chunk_f[c + 1];
-      const int kbase = g.kso[f0];
-      const int nks_c = g.kso[f1] - kbase;
-      const uint4 *stA = reinterpret_cast<const uint4 *>(stage + buf * kTc256Stage);
-      const uint2 *stB0 = reinterpret_cast<const uint2 *>(stage + buf * kTc256Stage + static_cast<size_t>(nks_c) * 512);
-      const uint2 *stB1 = stB0 + nks_c * 32;
-      for (int f = f0 + warp; f < f1; f += kTc256Warps) {
-        const int j1 = g.kso[f + 1] - kbase;
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int j = g.kso[f] - kbase; j < j1; ++j) {
-          const uint4 af = stA[j * 32 + lane];
-          mma16816<FP16>(d0, af, stB0[j * 32 + lane]);
-          mma16816<FP16>(d1, af, stB1[j * 32 + lane]);
-        }
-        // lane (g8, t4): d[0..1] = Re/Im Z(f), d[2..3] = Im/Re Z(M - f)
-        const int pf = z256_fold(f) ^ sw;
-        z0[pf] = pack_bf2(d0[0], d0[1]);
-        z1[pf] = pack_bf2(d1[0], d1[1]);
-        if (f != 0 && f != M / 2) {
-          const int pm = z256_fold(M - f) ^ sw;
-          z0[pm] = pack_bf2(d0[3], d0[2]);
-          z1[pm] = pack_bf2(d1[3], d1[2]);
-        }
-      }
-    }
-    if (__syncthreads_or(!ok)) {  // uniform: every thread leaves the loop
-      failed = true;
-      break;
-    }
-    if (tid == 0 && c + 2 < nch) issue(c + 2);
-  }
-  if (failed) {
-    if (tid == 0) {
-      atomicOr(a.err, 1);
-      // let the copies still in flight land before the CTA's memory goes
-      mbar_wait_bounded(full + (c & 1), static_cast<uint32_t>((c >> 1) & 1), a.wait_limit);
-      if (c + 1 < nch) mbar_wait_bounded(full + ((c + 1) & 1), static_cast<uint32_t>(((c + 1) >> 1) & 1), a.wait_limit);
-    }
-    return;
-  }
-
-  // ---------------- Phase 2: tensor-core inverse DFT, row maxima ----------------
+  // lane constants of phase 2
   uint32_t a1[16], b2[16];
   {
     const uint4 *fa = reinterpret_cast<const uint4 *>(g.dft16) + lane * 4;
@@ -375,23 +336,78 @@ __global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, 
   }
   TcLane Ln;
   tc_lane_init(Ln, tw, lane);
-  const int ref = kt * 8 + warp;  // pairs warp + 8 i: reference `warp` of the tile, row i
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int sw = 4 * g8 + t4;                 // z256_swz of both of this lane's phase-1 pairs
+  uint32_t *z0 = Zw + (8 * g8 + t4) * M;      // pair (row g8, reference t4)
+  uint32_t *z1 = z0 + 4 * M;                  // pair (row g8, reference 4 + t4)
   const int S = g.S;
-#pragma unroll 1
-  for (int i = 0; i < 8; ++i) {
-    const int pc = 8 * i + warp;
-    const int64_t row = rt * 8 + i;
-    const bool valid = row < a.rows && ref < a.K;
-    const int64_t img = rinfo[i].x;
-    const int s = rinfo[i].y;
-    float *dbg = (a.dbg_cc && valid) ? a.dbg_cc + ((img * a.K + ref) * S + s) * 2 * M : nullptr;
-    float vu, vm;
-    pair_idft_tc256(Zw + pc * M, z256_swz(pc), Ln, a1, b2, lane, vu, vm, dbg);
-    if (valid && lane == 0) {
-      float *rm = a.rowmax + (img * a.K + ref) * static_cast<int64_t>(S) * 2 + 2 * s;
-      rm[0] = vu;
-      rm[1] = g.mirror ? vm : -INFINITY;
+
+  int q = 0;  // global chunk index
+  for (int kt = 0; kt < ref_tiles; ++kt) {
+    // ---------------- Phase 1: tensor-core contraction ----------------
+    for (int c = 0; c < nch; ++c, ++q) {
+      const int buf = q & 1;
+      const bool ok = mbar_wait_bounded(full + buf, static_cast<uint32_t>((q >> 1) & 1),
+                                        q == 0 ? a.first_wait_limit : a.wait_limit);
+      if (ok) {
+        const int f0 = s_cf[c], f1 = s_cf[c + 1];
+        const int kbase = s_kso[f0];
+        const int nks_c = s_kso[f1] - kbase;
+        const uint4 *stA = reinterpret_cast<const uint4 *>(stage + buf * kTc256Stage) + lane;
+        const uint2 *stB0 = reinterpret_cast<const uint2 *>(stage + buf * kTc256Stage + static_cast<size_t>(nks_c) * 512) + lane;
+        const uint2 *stB1 = stB0 + nks_c * 32;
+        for (int f = f0 + warp; f < f1; f += kTc256Warps) {
+          const int jb = s_kso[f] - kbase, nj = s_kso[f + 1] - s_kso[f];  // 1..3 k-steps
+          float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) {
+            if (jj < nj) {
+              const int j = (jb + jj) * 32;
+              const uint4 af = stA[j];
+              mma16816<FP16>(d0, af, stB0[j]);
+              mma16816<FP16>(d1, af, stB1[j]);
+            }
+          }
+          // lane (g8, t4): d[0..1] = Re/Im Z(f), d[2..3] = Im/Re Z(M - f)
+          const int pf = z256_fold(f) ^ sw;
+          z0[pf] = pack_bf2(d0[0], d0[1]);
+          z1[pf] = pack_bf2(d1[0], d1[1]);
+          if (f != 0 && f != M / 2) {
+            const int pm = z256_fold(M - f) ^ sw;
+            z0[pm] = pack_bf2(d0[3], d0[2]);
+            z1[pm] = pack_bf2(d1[3], d1[2]);
+          }
+        }
+      }
+      if (__syncthreads_or(!ok)) {  // uniform: every thread leaves
+        if (tid == 0) {
+          atomicOr(a.err, 1);
+          // let the copies still in flight land before the CTA's memory goes
+          mbar_wait_bounded(full + (q & 1), static_cast<uint32_t>((q >> 1) & 1), a.wait_limit);
+          if (q + 1 < total)
+            mbar_wait_bounded(full + ((q + 1) & 1), static_cast<uint32_t>(((q + 1) >> 1) & 1), a.wait_limit);
+        }
+        return;
+      }
+      if (tid == 0 && q + 2 < total) issue(q + 2);
     }
+
+    // ---------------- Phase 2: tensor-core inverse DFT, row maxima ----------------
+    const int ref = kt * 8 + warp;  // pairs warp + 8 i: reference `warp` of the tile, row i
+    const int nvalid = ref < a.K ? static_cast<int>(min(static_cast<int64_t>(8), a.rows - rt * 8)) : 0;
+#pragma unroll 1
+    for (int i = 0; i < nvalid; ++i) {  // padding pairs are skipped (warp-uniform)
+      const int pc = 8 * i + warp;
+      const int2 ri = rinfo[i];
+      float *dbg = a.dbg_cc ? a.dbg_cc + ((static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y) * 2 * M : nullptr;
+      float vu, vm;
+      pair_idft_tc256(Zw + pc * M, z256_swz(pc), Ln, a1, b2, lane, vu, vm, dbg);
+      const float best = warp_max2(vu, vm, lane);
+      if ((lane & 15) == 0)
+        a.rowmax[((static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y) * 2 + (lane >> 4)] =
+            (lane && !g.mirror) ? -INFINITY : best;
+    }
+    __syncthreads();  // the next tile's contraction overwrites the pair buffers
   }
 }
 
@@ -729,8 +745,9 @@ static cudaError_t launch_tc256(const Geometry &g, const TcArgs &a, cudaStream_t
   }
   const int64_t row_tiles = (a.rows + kTile - 1) / kTile;
   if (row_tiles <= 0) return cudaSuccess;
-  dim3 grid((a.K + kTile - 1) / kTile, static_cast<unsigned>(row_tiles));
-  cc_tc256_kernel<FP16><<<grid, kTc256Threads, kTc256Smem, st>>>(g, a);
+  if (g.NCH > kTc256MaxChunks) return cudaErrorInvalidValue;
+  cc_tc256_kernel<FP16><<<static_cast<unsigned>(row_tiles), kTc256Threads, kTc256Smem, st>>>(
+      g, a, (a.K + kTile - 1) / kTile);
   return cudaGetLastError();
 }
 

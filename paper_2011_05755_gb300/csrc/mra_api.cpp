@@ -3,6 +3,7 @@
 // workspace ownership and the chunked launch sequence of Algorithm 1.
 #include "../../include/mra.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -311,6 +312,44 @@ int build_tables(mra_handle *h) {
       shifts[iy * nx + ix] = make_float2(static_cast<float>(-double(c.shift_range) + ix * double(c.shift_step)),
                                          static_cast<float>(-double(c.shift_range) + iy * double(c.shift_step)));
 
+  // Taps for integer shift grids (the sample position c0 + o in FP32, as the
+  // kernel would form it; an integer shift moves only the tap index).
+  std::vector<float4> taps;
+  int pad = -1;
+  {
+    bool integral = true;
+    for (const float2 &sv : shifts) integral = integral && sv.x == std::floor(sv.x) && sv.y == std::floor(sv.y);
+    int smax = 0;
+    for (const float2 &sv : shifts)
+      smax = std::max(smax, static_cast<int>(std::max(std::fabs(sv.x), std::fabs(sv.y))));
+    if (integral) {
+      const float c0 = 0.5f * static_cast<float>(c.L);
+      int lo = 0, hi = 0;
+      std::vector<int2> base(NS);
+      std::vector<float2> frac(NS);
+      for (int q = 0; q < NS; ++q) {
+        const float x = c0 + offs[q].x, y = c0 + offs[q].y;
+        const float xf = std::floor(x), yf = std::floor(y);
+        base[q] = make_int2(static_cast<int>(xf), static_cast<int>(yf));
+        frac[q] = make_float2(x - xf, y - yf);
+        lo = std::min(lo, std::min(base[q].x, base[q].y) - smax);
+        hi = std::max(hi, std::max(base[q].x, base[q].y) + 1 + smax - (c.L - 1));
+      }
+      const int need = std::max(-lo, hi);
+      if (need <= 8) {
+        pad = need <= 4 ? 4 : 8;  // a multiple of 4 keeps the interior float4-aligned
+        const int Lp = c.L + 2 * pad;
+        taps.resize(NS);
+        for (int q = 0; q < NS; ++q) {
+          const int idx = (base[q].y + pad) * Lp + (base[q].x + pad);
+          float fidx;
+          std::memcpy(&fidx, &idx, 4);
+          taps[q] = make_float4(fidx, frac[q].x, frac[q].y, 0.f);
+        }
+      }
+    }
+  }
+
   mra::Geometry &g = h->g;
   g.L = c.L;
   g.M = M;
@@ -324,6 +363,12 @@ int build_tables(mra_handle *h) {
   h->NB = NB;
   int rc;
   if ((rc = upload(h, offs, &g.offs, "ring offsets"))) return rc;
+  g.taps = nullptr;
+  g.pad = 0;
+  if (pad >= 0) {
+    if ((rc = upload(h, taps, &g.taps, "bilinear taps"))) return rc;
+    g.pad = pad;
+  }
   if ((rc = upload(h, rings, &g.rings, "ring table"))) return rc;
   if ((rc = upload(h, binpos, &g.binpos, "bin positions"))) return rc;
   if ((rc = upload(h, bweight, &g.bweight, "ring weights"))) return rc;

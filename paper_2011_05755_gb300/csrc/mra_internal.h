@@ -23,6 +23,12 @@ struct Geometry {
   int S;            // shifts
   int mirror;       // 0/1
   const float2 *offs;     // [NS]  r (cos theta_q, sin theta_q)
+  // Integer shift grids: bilinear taps of the unshifted sample positions in
+  // a copy of the image with a zero border of `pad` pixels (row length
+  // L + 2 pad); tap q = {index of the top-left neighbour (int bits), fx, fy}.
+  // Null when the shift grid is not integer or the border would exceed 8.
+  const float4 *taps;     // [NS] or null
+  int pad;
   const int4 *rings;      // [NR]  {N_r, sample offset, natural-bin offset, log2(N_r/2)}
   const int *binpos;      // [NBIN] padded position of (ring, f), ring-major natural order
   const float *bweight;   // [NBIN] reference-side weight of (ring, f)
