@@ -382,6 +382,16 @@ int build_tables(mra_handle *h) {
   if ((rc = upload(h, ksinfo, &g.ksinfo, "k-step table"))) return rc;
   if ((rc = upload(h, binpos16, &g.binpos16, "16-bit bin positions"))) return rc;
   {
+    // per-frequency bases: position of (ring i, f) = base[f] + i in both layouts
+    std::vector<int> kpos(H + 1), kpos16(H + 1);
+    for (int f = 0; f <= H; ++f) {
+      kpos[f] = fseg[f].x - first[f];
+      kpos16[f] = kso[f] * 16 - first[f];
+    }
+    if ((rc = upload(h, kpos, &g.kpos, "frequency bases"))) return rc;
+    if ((rc = upload(h, kpos16, &g.kpos16, "16-bit frequency bases"))) return rc;
+  }
+  {
     // whole frequencies per staging chunk of the M = 256 kernel, greedily
     std::vector<int> chunk_f(1, 0);
     for (int f = 0; f <= H; ++f) {

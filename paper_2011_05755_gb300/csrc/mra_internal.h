@@ -43,6 +43,8 @@ struct Geometry {
   const int *kso;         // [M/2 + 2]
   const int2 *ksinfo;     // [KS]
   const int *binpos16;    // [NBIN] position kso[f] * 16 + (ring - first ring of f)
+  const int *kpos;        // [M/2 + 1] binpos of (ring i, f) = kpos[f] + i
+  const int *kpos16;      // [M/2 + 1] binpos16 of (ring i, f) = kpos16[f] + i
   // BF16 mma fragments of the two 16-point DFT stages of the tensor-core
   // inverse angular DFT (M = 256): [0, 512) stage-1 A, [512, 1024) stage-2 B,
   // each [32 lanes][16 words].

@@ -52,6 +52,7 @@ float h_bweight[kMaxBins];
 float2 h_fwd[kMaxM], h_inv[kMaxM], h_ang[kMaxM];
 float2 h_shifts[kMaxShifts];
 int2 h_fseg[kMaxM / 2 + 1];
+int h_kpos[kMaxM / 2 + 1];
 
 // Error text goes to the caller's buffer (msg, msg_len), if one was given.
 thread_local char *g_msg = nullptr;
@@ -143,6 +144,7 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
     first[f] = i0;
     const int Rp = (NR - i0 + 1) & ~1;
     h_fseg[f] = make_int2(NB, Rp);
+    h_kpos[f] = NB - i0;  // bin (ring i, f) sits at h_kpos[f] + i
     NB += Rp;
     seg_max = Rp > seg_max ? Rp : seg_max;
   }
@@ -202,6 +204,7 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   float2 *d_shifts = reinterpret_cast<float2 *>(take(sizeof(float2) * S));
   float2 *d_ang = reinterpret_cast<float2 *>(take(sizeof(float2) * M));
   int2 *d_fseg = reinterpret_cast<int2 *>(take(sizeof(int2) * (H + 1)));
+  int *d_kpos = reinterpret_cast<int *>(take(sizeof(int) * (H + 1)));
   int *d_err = reinterpret_cast<int *>(take(sizeof(int)));
   const int Kpad = (K + mra::kTile - 1) / mra::kTile * mra::kTile;
   const size_t b_bytes = static_cast<size_t>(Kpad) * NB * sizeof(float2);
@@ -241,6 +244,7 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   MRA_COPY(d_shifts, h_shifts, sizeof(float2) * S);
   MRA_COPY(d_ang, h_ang, sizeof(float2) * M);
   MRA_COPY(d_fseg, h_fseg, sizeof(int2) * (H + 1));
+  MRA_COPY(d_kpos, h_kpos, sizeof(int) * (H + 1));
 #undef MRA_COPY
   g.offs = d_offs;
   g.rings = d_rings;
@@ -251,6 +255,7 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   g.shifts = d_shifts;
   g.angles = d_ang;
   g.fseg = d_fseg;
+  g.kpos = d_kpos;
 
   // The array keeps the previous call's data: padding bins of both spectra
   // layouts and the failure flag must read as zero.

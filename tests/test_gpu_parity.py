@@ -246,6 +246,38 @@ def test_workload_n100k_L76_K100_sampled(mra, prec):
     _check_poses_and_averages(mra, refs, imgs, cfg, sample=sample, precision=precision)
 
 
+@pytest.fixture(scope="module")
+def l128_case():
+    """The larger-box workload (L = 128, K = 200, rings 1..60, M = 512, 169
+    shifts): 600 images (several chunks and a ragged tail) and the oracle's
+    tables for two of them."""
+    w = synth.WORKLOADS["mra_n50k_L128_K200_shift6"]
+    refs, imgs, _, _ = synth.make_workload(w, n=600)
+    cfg = O.MRAConfig(w.L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror)
+    spec = O.reference_spectra(refs.double().numpy(), cfg)
+    sample = [0, 599]
+    tabs = {i: O.cc_table(imgs[i].double().numpy(), spec, cfg) for i in sample}
+    return w, refs, imgs, cfg, tabs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
+def test_workload_L128_K200_sampled(mra, l128_case, prec):
+    w, refs, imgs, cfg, tabs = l128_case
+    precision = {"fp32": mra.MRA_FP32, "bf16": mra.MRA_BF16_RESCORE, "fp16": mra.MRA_FP16_RESCORE}[prec]
+    al = mra.Aligner(w.L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, precision)
+    al.set_refs(refs.to(DEV))
+    gp = mra.decode_poses(al.align(imgs.to(DEV)))
+    al.close()
+    for i, tab in tabs.items():
+        p = O._pose_from_table(tab, cfg)
+        assert abs(gp["cc"][i] - p.cc) <= CC_TOL * abs(p.cc), (i, gp["cc"][i], p.cc)
+        got = (int(gp["k"][i]), int(gp["shift_idx"][i]), int(gp["mirror"][i]), int(gp["ang_idx"][i]))
+        if p.rel_gap > GAP:
+            assert got == (p.k, p.shift_idx, p.mirror, p.ang_idx), (i, got, p)
+        else:
+            assert tab[got] >= p.cc - CC_TOL * abs(p.cc)
+
+
 def test_chunking_and_ragged_tail_match_single_chunk(mra):
     refs, imgs = _inputs(32, 9, 23, 1.0, 1, seed=77)
     outs = []
