@@ -1,0 +1,151 @@
+// FP32 rescore of the precision-split path's candidate rows (north-star
+// precision split: the 8 rows (reference, shift, mirror) per image with the
+// largest 16-bit row maxima are recomputed from the image in FP32; the
+// argmax over them is the answer, Algorithm 1's reduction restricted to
+// those rows).
+#include "../../include/mra.h"
+#include "dev_util.cuh"
+#include "mra_internal.h"
+#include "pair_ifft.cuh"
+#include "ring_fft.cuh"
+
+namespace mra {
+
+// ---------------------------------------------------------------------------
+// FP32 rescore: for each candidate row of an image, resample at its shift,
+// ring-FFT, contract with its reference in FP32, inverse DFT; keep the best
+// (value, smallest index) over the candidates' angles as the argmax key.
+// One CTA per image.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a) {
+  constexpr int T = IfftShape<M>::T;
+  constexpr int U = IfftShape<M>::U;
+  extern __shared__ float4 smem_f4[];
+  const int L = g.L, NS = g.NS, S = g.S;
+  const int LL = L * L;
+  const int LLp = (LL + 3) & ~3;
+  const int64_t img = blockIdx.x;
+  float *im = reinterpret_cast<float *>(smem_f4);
+  float2 *twf = reinterpret_cast<float2 *>(im + LLp);
+  float2 *twi = twf + M;
+  float2 *Z = twi + M;
+  float2 *spec = Z + IfftShape<M>::P;
+  float *samp = reinterpret_cast<float *>(spec + ((g.NBIN + 1) & ~1));
+  const float c0 = 0.5f * static_cast<float>(L);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(a.imgs + img * LL + i);
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    twf[i] = g.fwd_tw[i];
+    twi[i] = g.inv_tw[i];
+  }
+  unsigned long long best = 0ull;
+  for (int c = 0; c < kTopRows; ++c) {
+    const int rowid = a.cand[img * kTopRows + c];
+    if (rowid < 0) continue;  // uniform over the CTA
+    const int m = rowid & 1;
+    const int rs = rowid >> 1;
+    const int s = rs % S;
+    const int k = rs / S;
+    __syncthreads();
+    const float2 sh = g.shifts[s];
+    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
+      const float2 o = g.offs[q];
+      samp[q] = bilinear_smem(im, L, c0 + sh.x + o.x, c0 + sh.y + o.y);
+    }
+    __syncthreads();
+    for (int ring = g.NR - 1 - warp; ring >= 0; ring -= 8) {
+      const int4 rd = g.rings[ring];
+      const int N = rd.x, H = N >> 1;
+      float2 *z = reinterpret_cast<float2 *>(samp + rd.y);
+      warp_fft_inplace(z, H, rd.w, M, twf, lane);
+      const int wstep = M / N;
+      for (int kx = lane; kx <= H; kx += 32) spec[rd.z + kx] = real_split(z, H, kx, twf[kx * wstep]);
+      __syncwarp();
+    }
+    __syncthreads();
+    // FP32 contraction with reference k for every frequency
+    const float2 *Bk = a.B + static_cast<int64_t>(k / kTile) * g.NB * kTile + (k % kTile);
+    for (int f = threadIdx.x; f <= M / 2; f += blockDim.x) {
+      float p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;
+      for (int ring = g.NR - 1; ring >= 0; --ring) {
+        const int4 rd = g.rings[ring];
+        if (rd.x / 2 < f) break;
+        const float2 A = spec[rd.z + f];
+        const float2 Bv = __ldg(Bk + static_cast<int64_t>(g.binpos[rd.z + f]) * kTile);
+        p1 = fmaf(A.x, Bv.x, p1);
+        p2 = fmaf(A.y, Bv.y, p2);
+        p3 = fmaf(A.x, Bv.y, p3);
+        p4 = fmaf(A.y, Bv.x, p4);
+      }
+      Z[f] = make_float2((p1 + p2) - (p3 + p4), (p3 - p4) + (p1 - p2));
+      if (f != 0 && f != M / 2) Z[M - f] = make_float2((p1 + p2) + (p3 + p4), (p1 - p2) - (p3 - p4));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int tt = lane % T;
+      const bool owner = lane < T;
+      float2 y[IfftShape<M>::KK][T];
+      pair_ifft<M>(Z, 0, Z, tt, owner, twi, y);
+      float v = -INFINITY;
+      uint32_t ang = 0xffffffffu;
+#pragma unroll
+      for (int kk = 0; kk < U / T; ++kk)
+#pragma unroll
+        for (int jj = 0; jj < T; ++jj) {
+          const int j = ifft_angle<M>(tt, kk, jj);
+          const float x = m ? y[kk][jj].y : y[kk][jj].x;
+          const uint32_t aj = m ? static_cast<uint32_t>((j + M / 2) & (M - 1)) : static_cast<uint32_t>(j);
+          if (x > v || (x == v && aj < ang)) {
+            v = x;
+            ang = aj;
+          }
+        }
+      unsigned long long key = owner ? make_key(v, static_cast<uint32_t>(rowid) * M + ang) : 0ull;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+        key = o > key ? o : key;
+      }
+      if (lane == 0 && key > best) best = key;
+    }
+  }
+  if (threadIdx.x == 0) a.best[img] = best;
+}
+
+size_t rescore_smem(const Geometry &g) {
+  const int T = g.M >= 256 ? 16 : g.M / 16;
+  const int P = T * (g.M / T + 1);
+  return static_cast<size_t>((g.L * g.L + 3) & ~3) * sizeof(float) + (2 * g.M + P) * sizeof(float2) +
+         static_cast<size_t>((g.NBIN + 1) & ~1) * sizeof(float2) + static_cast<size_t>(g.NS) * sizeof(float);
+}
+
+template <int M>
+static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
+  const size_t smem = rescore_smem(g);
+  static size_t attr_set = 0;
+  if (attr_set < smem) {
+    cudaError_t e =
+        cudaFuncSetAttribute(rescore_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    attr_set = smem;
+  }
+  rescore_kernel<M><<<static_cast<unsigned>(a.n), 256, smem, st>>>(g, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
+  if (a.n <= 0) return cudaSuccess;
+  switch (g.M) {
+    case 16: return launch_rescore_t<16>(g, a, st);
+    case 32: return launch_rescore_t<32>(g, a, st);
+    case 64: return launch_rescore_t<64>(g, a, st);
+    case 128: return launch_rescore_t<128>(g, a, st);
+    case 256: return launch_rescore_t<256>(g, a, st);
+    case 512: return launch_rescore_t<512>(g, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mra
