@@ -168,11 +168,27 @@ def _main():
     for name, r in runs.items():
         p = decode_poses(r["poses"])
         report[name] = {"history": r["history"], "ari_vs_truth": adjusted_rand_index(p["k"], truth.k)}
+    if args.compare and args.precision != "fp32":
+        # one pass of both paths from the same references: the precision split alone
+        for label, refs in (("initial_refs", refs0), ("final_fp32_refs", runs["fp32"]["refs"])):
+            got = {}
+            for name, code in ((args.precision, prec), ("fp32", MRA_FP32)):
+                al = Aligner(w.L, 1, 35, 1, w.shift_range, 1.0, 1, code)
+                al.set_refs(refs)
+                got[name] = decode_poses(al.align(imgs))
+                al.close()
+            a, b = got[args.precision], got["fp32"]
+            same_k = a["k"] == b["k"]
+            same_pose = same_k & (a["ang_idx"] == b["ang_idx"]) & (a["shift_idx"] == b["shift_idx"]) & (
+                a["mirror"] == b["mirror"])
+            report["same_refs_" + label] = {"class": float(np.mean(same_k)), "pose": float(np.mean(same_pose)),
+                                            "cc_rel_diff_median": float(np.median(np.abs(a["cc"] - b["cc"]) /
+                                                                                  np.maximum(np.abs(b["cc"]), 1e-30)))}
     if "fp32" in runs and len(runs) == 2:
         a = decode_poses(runs[args.precision]["poses"])
         b = decode_poses(runs["fp32"]["poses"])
         same_class = a["k"] == b["k"]
-        report["agreement"] = {
+        report["agreement_after_independent_runs"] = {
             "class": float(np.mean(same_class)),
             "ari_between_paths": adjusted_rand_index(a["k"], b["k"]),
             "pose_given_class": float(np.mean((a["ang_idx"] == b["ang_idx"]) & (a["shift_idx"] == b["shift_idx"])
