@@ -7,10 +7,13 @@ on the device, one set per (L, K).  The loop
 * admits arrived requests in arrival order while a slot is free and the
   stack fits the device-memory budget (a request larger than the whole budget
   is rejected with an error, never queued forever);
-* batches: the admitted head request takes along later queued requests with
-  the same (L, K), up to ``max_batch_images`` images, into one contiguous
+* serves a request in parts of at most ``part_images`` images, so that a
+  large request's parts run on several slots at once (or, with
+  ``requeue="back"``, so that small requests are served between them);
+* batches: the admitted head part takes along later queued parts with the
+  same (L, K), up to ``max_batch_images`` images, into one contiguous
   device stack and one ``mra_align`` call (images are independent, so a
-  request's poses do not depend on what it was batched with);
+  request's poses do not depend on how it was split or batched);
 * overlaps: every slot owns a CUDA stream and, per box size, a library handle
   with its own workspace; the reference spectra are transformed once per set
   and copied into a slot's handle on the device when the slot switches sets
@@ -60,6 +63,8 @@ class Request:
     poses: Optional[torch.Tensor] = None        # host int32 [n, 8] (mra_pose_t rows)
     error: str = ""
     batch_id: int = -1
+    parts_left: int = 0                         # parts issued or queued and not yet finished
+    next_off: int = 0                           # first image not yet given to a part
 
     @property
     def key(self) -> Tuple[int, int]:
@@ -74,57 +79,103 @@ class Request:
         return self.done - self.arrival
 
 
-class Scheduler:
-    """Admission and batching policy: FIFO head first, same-key followers batched in."""
+@dataclasses.dataclass
+class Part:
+    """Images [off, off + n) of one request: the unit the scheduler batches."""
+    req: Request
+    off: int
+    n: int
 
-    def __init__(self, hbm_budget: int, n_slots: int, max_batch_images: int):
-        if n_slots < 1 or hbm_budget <= 0 or max_batch_images < 1:
-            raise ValueError("n_slots, hbm_budget and max_batch_images must be positive")
+    @property
+    def key(self) -> Tuple[int, int]:
+        return self.req.key
+
+    @property
+    def device_bytes(self) -> int:
+        return self.n * (self.req.L * self.req.L * 4 + POSE_BYTES)
+
+
+class Scheduler:
+    """Admission and batching policy over request parts.
+
+    The head of the queue is admitted first (FIFO, no overtaking while it
+    waits for memory); queued parts with the same (L, K) are batched in up to
+    ``max_batch_images``.  With ``part_images`` > 0 a request is served in
+    parts of at most that many images; when a part is issued the request's
+    next part is queued at the front (``requeue="front"``: the parts of a
+    large request spread over the free slots and it finishes sooner) or at
+    the back (``"back"``: round robin, small requests are served between the
+    parts of a large one); 0 serves every request as one part.
+    """
+
+    def __init__(self, hbm_budget: int, n_slots: int, max_batch_images: int, part_images: int = 0,
+                 requeue: str = "front"):
+        if n_slots < 1 or hbm_budget <= 0 or max_batch_images < 1 or part_images < 0:
+            raise ValueError("n_slots, hbm_budget and max_batch_images must be positive, part_images >= 0")
+        if requeue not in ("front", "back"):
+            raise ValueError("requeue must be 'front' or 'back'")
+        self.requeue = requeue
         self.hbm_budget = int(hbm_budget)
         self.free_bytes = int(hbm_budget)
         self.free_slots = list(range(n_slots))
         self.max_batch_images = int(max_batch_images)
+        self.part_images = int(part_images)
         self.queue: collections.deque = collections.deque()
         self.rejected: List[Request] = []
         self._batches = 0
 
+    def _next_part(self, r: Request) -> Part:
+        n = r.n - r.next_off if self.part_images == 0 else min(self.part_images, r.n - r.next_off)
+        p = Part(r, r.next_off, n)
+        r.next_off += n
+        return p
+
     def arrive(self, r: Request) -> None:
-        if r.device_bytes > self.hbm_budget:
-            r.error = f"stack needs {r.device_bytes} bytes, more than the {self.hbm_budget}-byte device budget"
+        first = min(r.n, self.part_images) if self.part_images else r.n
+        need = first * (r.L * r.L * 4 + POSE_BYTES)
+        if need > self.hbm_budget:
+            r.error = f"a part needs {need} bytes, more than the {self.hbm_budget}-byte device budget"
             self.rejected.append(r)
             return
-        self.queue.append(r)
+        r.next_off = 0
+        r.parts_left = 1 if self.part_images == 0 else -(-r.n // self.part_images)
+        self.queue.append(self._next_part(r))
 
-    def next_batch(self) -> Optional[Tuple[int, List[Request]]]:
-        """Pop (slot, batch) if the head request can be admitted now, else None."""
+    def next_batch(self) -> Optional[Tuple[int, List[Part]]]:
+        """Pop (slot, batch of parts) if the head part can be admitted now, else None."""
         if not self.queue or not self.free_slots:
             return None
         head = self.queue[0]
         if head.device_bytes > self.free_bytes:
-            return None  # wait for memory: later requests do not overtake the head
+            return None  # wait for memory: later parts do not overtake the head
         self.queue.popleft()
         batch = [head]
         used, imgs = head.device_bytes, head.n
         keep = collections.deque()
         while self.queue:
-            r = self.queue.popleft()
-            if (r.key == head.key and imgs + r.n <= self.max_batch_images
-                    and used + r.device_bytes <= self.free_bytes):
-                batch.append(r)
-                used += r.device_bytes
-                imgs += r.n
+            p = self.queue.popleft()
+            if (p.key == head.key and imgs + p.n <= self.max_batch_images
+                    and used + p.device_bytes <= self.free_bytes):
+                batch.append(p)
+                used += p.device_bytes
+                imgs += p.n
             else:
-                keep.append(r)
+                keep.append(p)
         self.queue = keep
         self.free_bytes -= used
         slot = self.free_slots.pop(0)
-        for r in batch:
-            r.batch_id = self._batches
+        for p in batch:
+            p.req.batch_id = self._batches
+            if p.req.next_off < p.req.n:  # the request's next part
+                if self.requeue == "back":
+                    self.queue.append(self._next_part(p.req))
+                else:
+                    self.queue.appendleft(self._next_part(p.req))
         self._batches += 1
         return slot, batch
 
-    def release(self, slot: int, batch: Sequence[Request]) -> None:
-        self.free_bytes += sum(r.device_bytes for r in batch)
+    def release(self, slot: int, batch: Sequence[Part]) -> None:
+        self.free_bytes += sum(p.device_bytes for p in batch)
         self.free_slots.append(slot)
         self.free_slots.sort()
 
@@ -132,8 +183,8 @@ class Scheduler:
 class Server:
     """Drives a :class:`Scheduler` and an executor over a stream of requests.
 
-    The executor provides ``launch(slot, batch) -> token``, ``poll(token) ->
-    bool`` and ``finish(token)`` (copies results into the requests).
+    The executor provides ``launch(slot, parts) -> token``, ``poll(token) ->
+    bool`` and ``finish(token)`` (copies each part's results into its request).
     """
 
     def __init__(self, scheduler: Scheduler, executor, clock: Callable[[], float] = time.perf_counter,
@@ -161,11 +212,13 @@ class Server:
                     try:
                         self.exe.finish(tok)
                     except Exception as e:  # a failed batch fails its requests, not the server
-                        for r in batch:
-                            r.error = f"{type(e).__name__}: {e}"
+                        for p in batch:
+                            p.req.error = f"{type(e).__name__}: {e}"
                     t = self.clock() - t0
-                    for r in batch:
-                        r.done = t
+                    for p in batch:
+                        p.req.parts_left -= 1
+                        if p.req.parts_left == 0:
+                            p.req.done = t
                     self.sched.release(slot, batch)
                     progressed = True
                 else:
@@ -177,14 +230,17 @@ class Server:
                     break
                 slot, batch = nb
                 t = self.clock() - t0
-                for r in batch:
-                    r.admitted = t
+                for p in batch:
+                    if math.isnan(p.req.admitted):
+                        p.req.admitted = t
                 try:
                     inflight.append((self.exe.launch(slot, batch), slot, batch))
                 except Exception as e:
-                    for r in batch:
-                        r.error = f"{type(e).__name__}: {e}"
-                        r.done = self.clock() - t0
+                    for p in batch:
+                        p.req.error = f"{type(e).__name__}: {e}"
+                        p.req.parts_left -= 1
+                        if p.req.parts_left == 0:
+                            p.req.done = self.clock() - t0
                     self.sched.release(slot, batch)
                 progressed = True
             if not progressed:
@@ -247,7 +303,7 @@ class GpuExecutor:
         return self._Aligner(L, r1, r2, 1, self.geom["shift_range"], self.geom["shift_step"], self.geom["mirror"],
                              self.precision, self.chunk_images)
 
-    def launch(self, slot: int, batch: Sequence[Request]):
+    def launch(self, slot: int, batch: Sequence[Part]):
         from . import mra_align
         L, K = batch[0].key
         st = self.streams[slot]
@@ -257,14 +313,14 @@ class GpuExecutor:
         if self.loaded[slot].get(L) != K:
             h.copy_refs(self.owners[(L, K)], st)
             self.loaded[slot][L] = K
-        n = sum(r.n for r in batch)
+        n = sum(p.n for p in batch)
         with torch.cuda.stream(st):
             d_imgs = torch.empty((n, L, L), dtype=torch.float32, device=self.dev)
             d_poses = torch.empty((n, 8), dtype=torch.int32, device=self.dev)
             off = 0
-            for r in batch:
-                d_imgs[off:off + r.n].copy_(r.imgs, non_blocking=True)
-                off += r.n
+            for p in batch:
+                d_imgs[off:off + p.n].copy_(p.req.imgs[p.off:p.off + p.n], non_blocking=True)
+                off += p.n
             mra_align(h.h, d_imgs, d_poses, st)
             h_poses = torch.empty((n, 8), dtype=torch.int32, pin_memory=True)
             h_poses.copy_(d_poses, non_blocking=True)
@@ -279,12 +335,14 @@ class GpuExecutor:
     def finish(self, tok) -> None:
         from . import mra_sync
         slot = tok["slot"]
-        L = tok["batch"][0].L
+        L = tok["batch"][0].key[0]
         mra_sync(self.handles[slot][L].h, self.streams[slot])  # surfaces a device wait timeout as an error
         off = 0
-        for r in tok["batch"]:
-            r.poses = tok["h_poses"][off:off + r.n]
-            off += r.n
+        for p in tok["batch"]:
+            if p.req.poses is None:
+                p.req.poses = torch.empty((p.req.n, 8), dtype=torch.int32)
+            p.req.poses[p.off:p.off + p.n] = tok["h_poses"][off:off + p.n]
+            off += p.n
         tok["bufs"] = None
 
     def close(self):
@@ -350,7 +408,8 @@ def make_pools(boxes, pool_images: int, n_classes: int, shift: int, snr: float, 
 
 def run_stream(n_requests: int, loads: Sequence[float], precision: int, slots: int = 4,
                max_batch_images: int = 8192, hbm_budget: int = 32 << 30, calibration_requests: int = 40,
-               pool_images: int = 20000, seed: int = 4004, device: int = 0) -> dict:
+               pool_images: int = 20000, seed: int = 4004, device: int = 0, part_images: int = 0,
+               requeue: str = "front") -> dict:
     """Calibrate capacity with a burst of requests, then serve Poisson streams at ``loads`` x capacity."""
     dev = torch.device("cuda", device)
     pools, refs = make_pools(BOX_SIZES, pool_images, 50, 3, 0.1, seed, dev)
@@ -359,7 +418,7 @@ def run_stream(n_requests: int, loads: Sequence[float], precision: int, slots: i
 
     def serve(reqs):
         attach_stacks(reqs, pools, seed + 7)
-        return summarize(Server(Scheduler(hbm_budget, slots, max_batch_images), exe).run(reqs))
+        return summarize(Server(Scheduler(hbm_budget, slots, max_batch_images, part_images, requeue), exe).run(reqs))
 
     serve(draw_requests(min(8, calibration_requests), math.inf, seed + 2))  # first-use workspace allocation
     cal = serve(draw_requests(calibration_requests, math.inf, seed + 1))
@@ -367,7 +426,8 @@ def run_stream(n_requests: int, loads: Sequence[float], precision: int, slots: i
     capacity = cal["images_per_s"] / mean_n
     report = {"workload": "Poisson stream; n log-uniform 200..20000; L in {64,76,96,128} (rings 1..L/2-4); "
                           "K in {50,100,200}; shifts +-3 step 1; mirror on",
-              "slots": slots, "max_batch_images": max_batch_images, "hbm_budget_bytes": hbm_budget,
+              "slots": slots, "max_batch_images": max_batch_images, "part_images": part_images, "requeue": requeue,
+              "hbm_budget_bytes": hbm_budget,
               "calibration": cal, "capacity_requests_per_s": capacity, "runs": {}}
     for load in loads:
         reqs = draw_requests(n_requests, load * capacity, seed + int(round(load * 1000)))
@@ -389,11 +449,14 @@ def _main():
     ap.add_argument("--hbm-budget-gb", type=float, default=32.0)
     ap.add_argument("--calibration-requests", type=int, default=40)
     ap.add_argument("--pool-images", type=int, default=20000)
+    ap.add_argument("--part-images", type=int, default=0, help="0 serves each request as one part")
+    ap.add_argument("--requeue", default="front", choices=["front", "back"])
     ap.add_argument("--seed", type=int, default=4004)
     args = ap.parse_args()
     prec = {"fp32": MRA_FP32, "bf16": MRA_BF16_RESCORE, "fp16": MRA_FP16_RESCORE}[args.precision]
     rep = run_stream(args.requests, args.load, prec, args.slots, args.max_batch_images,
-                     int(args.hbm_budget_gb * 2**30), args.calibration_requests, args.pool_images, args.seed)
+                     int(args.hbm_budget_gb * 2**30), args.calibration_requests, args.pool_images, args.seed,
+                     part_images=args.part_images, requeue=args.requeue)
     rep["precision"] = args.precision
     print(json.dumps(rep))
 

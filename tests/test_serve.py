@@ -38,27 +38,30 @@ class FakeExecutor:
     def launch(self, slot, batch):
         if batch[0].key == self.fail_key:
             raise RuntimeError("injected launch failure")
-        n = sum(r.n for r in batch)
-        self.in_use += sum(r.device_bytes for r in batch)
+        n = sum(p.n for p in batch)
+        self.in_use += sum(p.device_bytes for p in batch)
         self.max_in_use = max(self.max_in_use, self.in_use)
         tok = {"end": self.clock.t + n * self.per_image, "batch": batch, "slot": slot}
-        self.log.append(("launch", self.clock.t, slot, [r.rid for r in batch]))
+        self.log.append(("launch", self.clock.t, slot, [p.req.rid for p in batch]))
         return tok
 
     def poll(self, tok):
         return self.clock.t >= tok["end"]
 
     def finish(self, tok):
-        self.in_use -= sum(r.device_bytes for r in tok["batch"])
-        for r in tok["batch"]:
-            r.poses = np.full((r.n, 8), r.rid)
-        self.log.append(("finish", self.clock.t, tok["slot"], [r.rid for r in tok["batch"]]))
+        self.in_use -= sum(p.device_bytes for p in tok["batch"])
+        for p in tok["batch"]:
+            if p.req.poses is None:
+                p.req.poses = np.full((p.req.n, 8), -1)
+            p.req.poses[p.off:p.off + p.n] = p.req.rid
+        self.log.append(("finish", self.clock.t, tok["slot"], [p.req.rid for p in tok["batch"]]))
 
 
-def _run(reqs, budget, slots, max_batch, per_image=1e-4, fail_key=None):
+def _run(reqs, budget, slots, max_batch, per_image=1e-4, fail_key=None, part_images=0, requeue="front"):
     clk = SimClock()
     exe = FakeExecutor(clk, per_image, fail_key)
-    srv = Server(Scheduler(budget, slots, max_batch), exe, clock=clk, idle_sleep=1e-4, sleep=clk.sleep)
+    srv = Server(Scheduler(budget, slots, max_batch, part_images, requeue), exe, clock=clk, idle_sleep=1e-4,
+                 sleep=clk.sleep)
     srv.run(reqs)
     return exe
 
@@ -120,6 +123,32 @@ def test_head_is_not_overtaken_and_oversized_is_rejected():
     assert order.index(1) < order.index(2)    # FIFO: the small request waits behind the head
 
 
+def test_parts_round_robin_interleaves_small_requests():
+    # a large request first, then small ones arriving just after it, one slot
+    reqs = [Request(0, 32, 4, 1000, 0.0)] + [Request(i, 48, 4, 50, 0.001 * i) for i in range(1, 4)]
+    exe = _run(reqs, 10**9, slots=1, max_batch=10**6, part_images=300, requeue="back")
+    for r in reqs:
+        assert not r.error and (r.poses == r.rid).all()   # every image served exactly by its own request
+    # served whole, request 0 would finish before the small ones start; in parts they finish first
+    assert all(reqs[i].done < reqs[0].done for i in (1, 2, 3))
+    launched = [e[3] for e in exe.log if e[0] == "launch"]
+    assert sum(1 for b in launched if 0 in b) == 4       # ceil(1000 / 300) parts
+    fifo = [Request(0, 32, 4, 1000, 0.0)] + [Request(i, 48, 4, 50, 0.001 * i) for i in range(1, 4)]
+    _run(fifo, 10**9, slots=1, max_batch=10**6, part_images=0)
+    assert all(fifo[i].done > fifo[0].done for i in (1, 2, 3))
+
+
+def test_parts_front_spread_a_large_request_over_the_slots():
+    whole = [Request(0, 32, 4, 1200, 0.0)]
+    _run(whole, 10**9, slots=4, max_batch=10**6, part_images=0)
+    split = [Request(0, 32, 4, 1200, 0.0)]
+    exe = _run(split, 10**9, slots=4, max_batch=300, part_images=300, requeue="front")
+    assert (split[0].poses == 0).all()
+    slots = {e[2] for e in exe.log if e[0] == "launch"}
+    assert len(slots) == 4                                   # the four parts ran side by side
+    assert split[0].done < 0.5 * whole[0].done
+
+
 def test_failed_batch_fails_only_its_requests():
     reqs = [Request(0, 32, 4, 50, 0.0), Request(1, 48, 8, 50, 0.0), Request(2, 32, 4, 50, 0.0)]
     _run(reqs, 10**9, slots=2, max_batch=10**6, fail_key=(48, 8))
@@ -157,7 +186,7 @@ def test_results_same_alone_and_in_the_mix(mra, prec):
     exe = GpuExecutor(sets, 3, precision, chunk_images=256)
     mix = fresh()
     attach_stacks(mix, pools, 5)
-    Server(Scheduler(2**30, 3, 700), exe).run(mix)
+    Server(Scheduler(2**30, 3, 700, part_images=90), exe).run(mix)
     assert all(not r.error for r in mix)
     assert len({r.batch_id for r in mix}) < len(mix)          # something was batched
     for r in mix:
