@@ -365,11 +365,37 @@ def main():
         po_line["frac"] = po_line["achieved"] / po_line["peak"]
         roofline, other = (cc_line, po_line) if cc["ms"] >= po["ms"] else (po_line, cc_line)
         roofline = dict(roofline, other_kernel=other)
+        # whole-step lower bound: each unit's algorithmic work at its peak
+        pairs = n * S * K
+        rows = n * S
+        L2px = L * L * 4
+        hbm_peak = peaks.get("hbm_gbs", 6697.0)
+        half = prec_code != mra.MRA_FP32
+        a_bytes = info["n_bins_padded"] * 8 if not half else sum(
+            -(-sum(1 for _, nr in rings if nr // 2 >= f) // 16) for f in range(info["M"] // 2 + 1)) * 64
+        t_tensor = pairs * (f_con + (f_ifft if info["M"] == 256 else 0)) / (tpeak * 1e12) if half else 0.0
+        fp32_flops = rows * f_row                                   # polar resampling + ring FFTs
+        if not half:
+            fp32_flops += pairs * (f_con + f_ifft)                  # FP32 contraction + inverse DFT
+        else:
+            if info["M"] != 256:
+                fp32_flops += pairs * f_ifft                        # FP32 inverse DFT of the 16-bit path
+            fp32_flops += n * 8 * (f_row + f_con + f_ifft)          # rescore of 8 rows per image
+        t_fp32 = fp32_flops / (alu_peak * 1e12)
+        hbm_bytes = 2 * n * L2px + 2 * rows * a_bytes + (pairs * 16 if half else 0)
+        t_hbm = hbm_bytes / (hbm_peak * 1e9)
+        bound_ms = 1000.0 * max(t_tensor, t_fp32, t_hbm)
+        step_roof = {"t_tensor_ms": 1000.0 * t_tensor, "t_fp32_ms": 1000.0 * t_fp32, "t_hbm_ms": 1000.0 * t_hbm,
+                     "bound_ms": bound_ms, "ms_per_step": ms_step, "frac": bound_ms / ms_step,
+                     "note": "each unit's algorithmic work per step at its peak (tensor: contraction and, for "
+                             "M = 256, inverse-DFT flops at the BF16 peak; FP32: polar rows, FP32 contraction / "
+                             "inverse DFT and the 8 rescored rows per image; HBM: stack read twice, spectra "
+                             "written and read once, row maxima); frac = the largest / measured step time"}
         tensor = None
         if tensor:
             roofline["tensor"] = tensor
         return {"label": label, "al": al, "value": n * world / (ms_step / 1000.0), "ms_step": ms_step,
-                "prof": prof, "roofline": roofline, "clocks": clk, "info": info,
+                "prof": prof, "roofline": roofline, "clocks": clk, "info": info, "step_roofline": step_roof,
                 "gpu_launches": sum(v["launches"] for v in prof.values())}
 
     prec_label = args.precision
@@ -430,13 +456,14 @@ def main():
                        "step": "set_refs + align + class average",
                        "l2": "inputs (2.3 GB/GPU) larger than L2; no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "stages": prof, "roofline": roofline,
-            "cpu_baseline": cpu_line, "clocks": clk, "serving": serving,
+            "cpu_baseline": cpu_line, "clocks": clk, "serving": serving, "step_roofline": main_res["step_roofline"],
         }
         if cmp_res is not None:
             line["fp32_path"] = {"value": cmp_res["value"], "ms_per_step": cmp_res["ms_step"],
                                  "speedup_of_headline_path": value / cmp_res["value"],
                                  "roofline": cmp_res["roofline"], "stages": cmp_res["prof"],
-                                 "gpu_launches": cmp_res["gpu_launches"], "clocks": cmp_res["clocks"]}
+                                 "gpu_launches": cmp_res["gpu_launches"], "clocks": cmp_res["clocks"],
+                                 "step_roofline": cmp_res["step_roofline"]}
         print(json.dumps(line), flush=True)
     al.close()
     if world > 1:
