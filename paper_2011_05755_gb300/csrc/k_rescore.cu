@@ -32,14 +32,17 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
   float2 *Z = twi + M;
   float2 *spec = Z + IfftShape<M>::P;
   float *samp = reinterpret_cast<float *>(spec + ((g.NBIN + 1) & ~1));
+  int4 *s_rings = reinterpret_cast<int4 *>((reinterpret_cast<uintptr_t>(samp + g.NS) + 15) & ~uintptr_t(15));  // [NR]
   const float c0 = 0.5f * static_cast<float>(L);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int NR = g.NR;
 
   for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(a.imgs + img * LL + i);
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     twf[i] = g.fwd_tw[i];
     twi[i] = g.inv_tw[i];
   }
+  for (int i = threadIdx.x; i < NR; i += blockDim.x) s_rings[i] = g.rings[i];
   unsigned long long best = 0ull;
   for (int c = 0; c < kTopRows; ++c) {
     const int rowid = a.cand[img * kTopRows + c];
@@ -55,8 +58,8 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
       samp[q] = bilinear_smem(im, L, c0 + sh.x + o.x, c0 + sh.y + o.y);
     }
     __syncthreads();
-    for (int ring = g.NR - 1 - warp; ring >= 0; ring -= 8) {
-      const int4 rd = g.rings[ring];
+    for (int ring = NR - 1 - warp; ring >= 0; ring -= 8) {
+      const int4 rd = s_rings[ring];
       const int N = rd.x, H = N >> 1;
       float2 *z = reinterpret_cast<float2 *>(samp + rd.y);
       warp_fft_inplace(z, H, rd.w, M, twf, lane);
@@ -65,22 +68,43 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
       __syncwarp();
     }
     __syncthreads();
-    // FP32 contraction with reference k for every frequency
+    // FP32 contraction with reference k for every frequency: two threads per
+    // frequency (alternate rings, partial sums combined by a shuffle), the
+    // reference loads of four rings in flight at a time
     const float2 *Bk = a.B + static_cast<int64_t>(k / kTile) * g.NB * kTile + (k % kTile);
-    for (int f = threadIdx.x; f <= M / 2; f += blockDim.x) {
+    for (int it0 = 0; it0 < 2 * (M / 2 + 1); it0 += blockDim.x) {  // uniform trip count (shuffles below)
+      const int it = it0 + threadIdx.x;
+      const bool active = it < 2 * (M / 2 + 1);
+      const int f = active ? it >> 1 : 0, half = it & 1;
       float p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;
-      for (int ring = g.NR - 1; ring >= 0; --ring) {
-        const int4 rd = g.rings[ring];
-        if (rd.x / 2 < f) break;
-        const float2 A = spec[rd.z + f];
-        const float2 Bv = __ldg(Bk + static_cast<int64_t>(g.binpos[rd.z + f]) * kTile);
-        p1 = fmaf(A.x, Bv.x, p1);
-        p2 = fmaf(A.y, Bv.y, p2);
-        p3 = fmaf(A.x, Bv.y, p3);
-        p4 = fmaf(A.y, Bv.x, p4);
+      if (active) {
+        // rings with N_r / 2 >= f are a suffix [lo, NR) of the (ascending) ring list
+        int lo = 0, hi = NR;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (s_rings[mid].x / 2 < f) lo = mid + 1;
+          else hi = mid;
+        }
+        const float2 *Bf = Bk + static_cast<int64_t>(g.kpos[f]) * kTile;  // bin (ring, f) at kpos[f] + ring
+#pragma unroll 4
+        for (int ring = NR - 1 - half; ring >= lo; ring -= 2) {
+          const float2 A = spec[s_rings[ring].z + f];
+          const float2 Bv = __ldg(Bf + static_cast<int64_t>(ring) * kTile);
+          p1 = fmaf(A.x, Bv.x, p1);
+          p2 = fmaf(A.y, Bv.y, p2);
+          p3 = fmaf(A.x, Bv.y, p3);
+          p4 = fmaf(A.y, Bv.x, p4);
+        }
       }
-      Z[f] = make_float2((p1 + p2) - (p3 + p4), (p3 - p4) + (p1 - p2));
-      if (f != 0 && f != M / 2) Z[M - f] = make_float2((p1 + p2) + (p3 + p4), (p1 - p2) - (p3 - p4));
+      // items 2f and 2f + 1 are neighbouring lanes of one warp
+      p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+      p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
+      p3 += __shfl_xor_sync(0xffffffffu, p3, 1);
+      p4 += __shfl_xor_sync(0xffffffffu, p4, 1);
+      if (active && half == 0) {
+        Z[f] = make_float2((p1 + p2) - (p3 + p4), (p3 - p4) + (p1 - p2));
+        if (f != 0 && f != M / 2) Z[M - f] = make_float2((p1 + p2) + (p3 + p4), (p1 - p2) - (p3 - p4));
+      }
     }
     __syncthreads();
     if (warp == 0) {
@@ -118,7 +142,8 @@ size_t rescore_smem(const Geometry &g) {
   const int T = g.M >= 256 ? 16 : g.M / 16;
   const int P = T * (g.M / T + 1);
   return static_cast<size_t>((g.L * g.L + 3) & ~3) * sizeof(float) + (2 * g.M + P) * sizeof(float2) +
-         static_cast<size_t>((g.NBIN + 1) & ~1) * sizeof(float2) + static_cast<size_t>(g.NS) * sizeof(float);
+         static_cast<size_t>((g.NBIN + 1) & ~1) * sizeof(float2) + static_cast<size_t>(g.NS) * sizeof(float) + 16 +
+         static_cast<size_t>(g.NR) * sizeof(int4);
 }
 
 template <int M>
