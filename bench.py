@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the stack size (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="synthetic workload (default: the 100,000-particle bench stack; the others are for "
+                         "extra measurements, e.g. mra_n50k_L128_K200_shift6)")
     ap.add_argument("--serve-requests", type=int, default=60,
                     help="requests in the serving run (Poisson stream at 0.7 x capacity); 0 skips it")
     return ap.parse_args()
@@ -185,7 +188,7 @@ def run_reference(args):
         return 0
     import numpy as np
     import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[args.workload]
     sample = 16
     refs, imgs, _, _ = synth.make_workload(w, n=max(sample, 64))
     refs_np = refs.double().numpy()
@@ -200,7 +203,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": w.n, "L": w.L, "K": w.K, "S": 81, "rings": "1..35",
+            "config": {"workload": args.workload, "n": w.n, "L": w.L, "K": w.K,
+                       "S": int(round(2 * w.shift_range / w.shift_step + 1)) ** 2,
+                       "rings": f"{w.first_ring}..{w.last_ring}",
                        "mirror": 1, "path": "FP64 oracle (explicit DFT sums)",
                        "step": f"{sample} images per step, scaled to the stack"},
             "cpu_baseline": {"value": value, "unit": "images/s", "cores": times[-1]["cores"], "kind": "oracle",
@@ -234,7 +239,7 @@ def main():
     import paper_2011_05755_gb300 as mra
     from paper_2011_05755_gb300.shard import allreduce_class_sums
     import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[args.workload]
     n = args.n or w.n
     prec = {"fp32": mra.MRA_FP32, "bf16": mra.MRA_BF16_RESCORE, "fp16": mra.MRA_FP16_RESCORE}[args.precision]
 
@@ -450,11 +455,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16+f32", "fp16": "f16+f32"}[args.precision],
             "data": "synthetic (seeded Gaussian-blob references and particles, SNR 0.1)",
-            "config": {"workload": WORKLOAD, "n_per_gpu": n, "L": L, "K": K, "S": S, "rings": "1..35", "M": info["M"],
+            "config": {"workload": args.workload, "n_per_gpu": n, "L": L, "K": K, "S": S,
+                       "rings": f"{w.first_ring}..{w.last_ring}", "M": info["M"],
                        "mirror": 1, "path": {"fp32": "FP32", "bf16": "BF16 contraction + FP32 rescore of top-8 rows",
                                              "fp16": "FP16 contraction + FP32 rescore of top-8 rows"}[args.precision],
                        "step": "set_refs + align + class average",
-                       "l2": "inputs (2.3 GB/GPU) larger than L2; no flush"},
+                       "l2": f"inputs ({n * L * L * 4 / 1e9:.1f} GB/GPU) larger than L2; no flush"},
             "e2e": e2e, "gpu_launches": gpu_launches, "stages": prof, "roofline": roofline,
             "cpu_baseline": cpu_line, "clocks": clk, "serving": serving, "step_roofline": main_res["step_roofline"],
         }

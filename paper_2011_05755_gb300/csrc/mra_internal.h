@@ -55,7 +55,7 @@ struct Geometry {
   const int *chunk_f;     // [NCH + 1]
 };
 
-constexpr int kTc256ChunkKs = 20;
+constexpr int kTc256ChunkKs = 22;
 
 struct PolarArgs {
   const float *imgs;   // [n][L][L]
