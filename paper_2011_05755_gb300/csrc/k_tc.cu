@@ -619,18 +619,6 @@ static cudaError_t launch_tc_t(const Geometry &g, const TcArgs &a, cudaStream_t 
   return cudaGetLastError();
 }
 
-size_t cc_tc_smem(int M, int ks_max) {
-  switch (M) {
-    case 16: return TcShape<16, 8>::smem(ks_max);
-    case 32: return TcShape<32, 8>::smem(ks_max);
-    case 64: return TcShape<64, 8>::smem(ks_max);
-    case 128: return TcShape<128, 8>::smem(ks_max);
-    case 256: return kTc256Smem;
-    case 512: return TcShape<512, 4>::smem(ks_max);
-    default: return 0;
-  }
-}
-
 template <bool FP16>
 static cudaError_t launch_tc256(const Geometry &g, const TcArgs &a, cudaStream_t st) {
   static bool attr_set = false;

@@ -108,7 +108,6 @@ struct RescoreArgs {
 
 cudaError_t launch_refs16(const Geometry &g, const float2 *B, int ktiles, uint2 *B16, bool fp16, cudaStream_t st);
 cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStream_t st);
-size_t cc_tc_smem(int M, int ks_max);
 cudaError_t launch_top8(const float *rowmax, int64_t n, int nrows, int *cand, cudaStream_t st);
 cudaError_t launch_rescore(const Geometry &g, const RescoreArgs &a, cudaStream_t st);
 size_t rescore_smem(const Geometry &g);
@@ -116,7 +115,6 @@ size_t rescore_smem(const Geometry &g);
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st);
 cudaError_t launch_cc_fp32(const Geometry &g, const CCArgs &a, cudaStream_t st);
-size_t cc_fp32_smem(int M, int seg_max);  // dynamic shared memory of the FP32 kernel
 cudaError_t launch_decode(const Geometry &g, const unsigned long long *best, int64_t n, int K,
                           void *poses, cudaStream_t st);
 int cc_threads_per_pair(int M);
