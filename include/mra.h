@@ -60,7 +60,7 @@ enum mra_status {
     MRA_ENOMEM = 3,      /* device or host allocation failed                      */
     MRA_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed           */
     MRA_ETIMEOUT = 5,    /* a bounded device-side wait gave up                    */
-    MRA_EUNSUPPORTED = 6 /* valid request this build does not implement           */
+    MRA_EUNSUPPORTED = 6 /* valid request the library does not implement          */
 };
 
 enum mra_precision {

@@ -1,8 +1,7 @@
-// FP32 rescore of the precision-split path's candidate rows (north-star
-// precision split: the 8 rows (reference, shift, mirror) per image with the
-// largest 16-bit row maxima are recomputed from the image in FP32; the
-// argmax over them is the answer, Algorithm 1's reduction restricted to
-// those rows).
+// FP32 rescore of the precision-split path's candidate rows: the 8 rows
+// (reference, shift, mirror) per image with the largest 16-bit row maxima
+// are recomputed from the image in FP32, and the argmax over them is the
+// answer (Algorithm 1's reduction restricted to those rows).
 #include "../../include/mra.h"
 #include "dev_util.cuh"
 #include "mra_internal.h"
