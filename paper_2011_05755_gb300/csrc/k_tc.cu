@@ -15,8 +15,9 @@
 //
 // For M = 256 (rings up to 40) the per-pair angular state is kept as BF16 in
 // shared memory and the inverse angular DFT runs on tensor cores too
-// (cc_tc256_kernel); for other M the state stays FP32 and the inverse DFT
-// runs in FP32 (cc_tc_kernel).  Either way the row maxima select the 8 rows
+// (cc_tc256_kernel); for M = 512 the state is BF16 and the inverse DFT runs
+// in FP32 (cc_tc512_kernel); for M <= 128 the state stays FP32
+// (cc_tc_kernel).  Either way the row maxima select the 8 rows
 // (reference, shift, mirror) per image that the rescore kernel recomputes
 // from scratch in FP32; its argmax is the answer.
 #include <cuda_bf16.h>
@@ -411,6 +412,203 @@ __global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, 
   }
 }
 
+// M = 512 kernel (rings up to 81): the tile walk and chunked staging of the
+// M = 256 kernel with one CTA of 16 warps per SM (the BF16 spectra of the
+// 64 pairs take 128 KB) and chunks of up to kTc512ChunkKs k-steps.
+// Spectrum word of Z(f) in a pair's 512-word buffer: f ^ s with
+// s = 4 (pair / 8) + (pair % 4) < 32, so the contraction's stores (32 lanes,
+// 32 pairs, one f) hit distinct banks.  Phase 2: a half-warp per pair (rows
+// i and i + 4 of one reference in the two halves of a warp), FP32 inverse DFT
+// from the BF16 spectrum in the factorisation 512 = 16 x 32: thread t loads
+// Z(t + 16 a), a = 0..31, runs a length-32 register DFT, applies
+// exp(2 pi i t k / 512), writes its row of the 16 x 32 intermediate back
+// into the pair's buffer as BF16 words (row t, word k ^ lane), and finishes
+// with length-16 DFTs over the columns k = t and t + 16.  All these shared
+// accesses are bank-conflict free: the two half-warps always use opposite
+// halves of the banks.
+constexpr int kTc512Warps = 16;
+constexpr int kTc512Threads = 32 * kTc512Warps;
+constexpr int kTc512MaxChunks = 48;
+constexpr size_t kTc512Stage = static_cast<size_t>(kTc512ChunkKs) * 1024;
+constexpr size_t kTc512Smem = 2 * kTc512Stage + 64 * 512 * sizeof(uint32_t) + 512 * sizeof(float2) +
+                              2 * sizeof(uint64_t) + 8 * sizeof(int2) + (258 + kTc512MaxChunks + 2) * sizeof(int);
+static_assert(kTc512Smem <= 232448, "M = 512 kernel exceeds 227 KB of shared memory");
+
+__device__ __forceinline__ float2 unpack_bf2(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+template <bool FP16>
+__global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, TcArgs a, int ref_tiles) {
+  constexpr int M = 512, PAIRS = 64, NF = M / 2 + 1;
+  extern __shared__ float4 smem_f4[];
+  unsigned char *stage = reinterpret_cast<unsigned char *>(smem_f4);
+  uint32_t *Zw = reinterpret_cast<uint32_t *>(stage + 2 * kTc512Stage);  // [64 pairs][512 words]
+  float2 *tw = reinterpret_cast<float2 *>(Zw + PAIRS * M);
+  uint64_t *full = reinterpret_cast<uint64_t *>(tw + M);
+  int2 *rinfo = reinterpret_cast<int2 *>(full + 2);  // {image, shift} of the tile's rows
+  int *s_kso = reinterpret_cast<int *>(rinfo + 8);   // [NF + 1]
+  int *s_cf = s_kso + NF + 1;                        // [NCH + 1]
+
+  const int64_t rt = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nch = g.NCH;
+  const int total = ref_tiles * nch;
+  for (int i = tid; i < M; i += kTc512Threads) tw[i] = g.inv_tw[i];
+  for (int i = tid; i <= NF; i += kTc512Threads) s_kso[i] = g.kso[i];
+  for (int i = tid; i <= nch; i += kTc512Threads) s_cf[i] = g.chunk_f[i];
+  if (tid < 8) {
+    const int64_t row = rt * 8 + tid;
+    const int img = static_cast<int>(static_cast<uint32_t>(row) / static_cast<uint32_t>(g.S));  // rows < 2^31
+    rinfo[tid] = make_int2(img, static_cast<int>(row - static_cast<int64_t>(img) * g.S));
+  }
+  if (tid == 0) {
+    mbar_init(full, 1);
+    mbar_init(full + 1, 1);
+  }
+  mbar_init_fence();
+  __syncthreads();
+
+  auto issue = [&](int q) {  // thread 0: stage chunk q % nch of reference tile q / nch into buffer q & 1
+    const int kt = q / nch, c = q - kt * nch;
+    const int k0 = s_kso[s_cf[c]];
+    const uint32_t nks = static_cast<uint32_t>(s_kso[s_cf[c + 1]] - k0);
+    unsigned char *dst = stage + (q & 1) * kTc512Stage;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(full + (q & 1), nks * 1024u);
+    bulk_g2s(dst, a.A16 + (rt * g.KS + k0) * 32, nks * 512u, full + (q & 1));
+    bulk_g2s(dst + nks * 512u, a.B16 + ((static_cast<int64_t>(kt) * 2) * g.KS + k0) * 32, nks * 256u, full + (q & 1));
+    bulk_g2s(dst + nks * 768u, a.B16 + ((static_cast<int64_t>(kt) * 2 + 1) * g.KS + k0) * 32, nks * 256u,
+             full + (q & 1));
+  };
+  if (tid == 0) {
+    issue(0);
+    if (total > 1) issue(1);
+  }
+
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int sw = 4 * g8 + t4;              // spectrum swizzle of both of this lane's phase-1 pairs
+  uint32_t *z0 = Zw + (8 * g8 + t4) * M;   // pair (row g8, reference t4)
+  uint32_t *z1 = z0 + 4 * M;               // pair (row g8, reference 4 + t4)
+  const int S = g.S;
+  const int hw = lane >> 4, t = lane & 15;  // phase 2: half-warp, thread within the pair's group
+
+  int q = 0;  // global chunk index
+  for (int kt = 0; kt < ref_tiles; ++kt) {
+    // ---------------- Phase 1: tensor-core contraction ----------------
+    for (int c = 0; c < nch; ++c, ++q) {
+      const int buf = q & 1;
+      const bool ok = mbar_wait_bounded(full + buf, static_cast<uint32_t>((q >> 1) & 1),
+                                        q == 0 ? a.first_wait_limit : a.wait_limit);
+      if (ok) {
+        const int f0 = s_cf[c], f1 = s_cf[c + 1];
+        const int kbase = s_kso[f0];
+        const int nks_c = s_kso[f1] - kbase;
+        const uint4 *stA = reinterpret_cast<const uint4 *>(stage + buf * kTc512Stage) + lane;
+        const uint2 *stB0 =
+            reinterpret_cast<const uint2 *>(stage + buf * kTc512Stage + static_cast<size_t>(nks_c) * 512) + lane;
+        const uint2 *stB1 = stB0 + nks_c * 32;
+        for (int f = f0 + warp; f < f1; f += kTc512Warps) {
+          const int jb = s_kso[f] - kbase, nj = s_kso[f + 1] - s_kso[f];  // 1..6 k-steps
+          float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int jj = 0; jj < kTc512MaxKsPerF; ++jj) {
+            if (jj < nj) {
+              const int j = (jb + jj) * 32;
+              const uint4 af = stA[j];
+              mma16816<FP16>(d0, af, stB0[j]);
+              mma16816<FP16>(d1, af, stB1[j]);
+            }
+          }
+          // lane (g8, t4): d[0..1] = Re/Im Z(f), d[2..3] = Im/Re Z(M - f)
+          const int pf = f ^ sw;
+          z0[pf] = pack_bf2(d0[0], d0[1]);
+          z1[pf] = pack_bf2(d1[0], d1[1]);
+          if (f != 0 && f != M / 2) {
+            const int pm = (M - f) ^ sw;
+            z0[pm] = pack_bf2(d0[3], d0[2]);
+            z1[pm] = pack_bf2(d1[3], d1[2]);
+          }
+        }
+      }
+      if (__syncthreads_or(!ok)) {  // uniform: every thread leaves
+        if (tid == 0) {
+          atomicOr(a.err, 1);
+          // let the copies still in flight land before the CTA's memory goes
+          mbar_wait_bounded(full + (q & 1), static_cast<uint32_t>((q >> 1) & 1), a.wait_limit);
+          if (q + 1 < total)
+            mbar_wait_bounded(full + ((q + 1) & 1), static_cast<uint32_t>(((q + 1) >> 1) & 1), a.wait_limit);
+        }
+        return;
+      }
+      if (tid == 0 && q + 2 < total) issue(q + 2);
+    }
+
+    // ---------------- Phase 2: FP32 inverse DFT from the BF16 spectra, row maxima ----------------
+    const int refl = warp & 7;
+    const int ref = kt * 8 + refl;
+    if (ref < a.K) {  // warp-uniform: padding references are skipped
+#pragma unroll 1
+      for (int r = 0; r < 2; ++r) {
+        const int i = 2 * (warp >> 3) + r + 4 * hw;  // row of this half-warp's pair
+        uint32_t *zp = Zw + (8 * i + refl) * M;
+        const int s = 4 * i + (refl & 3);            // spectrum swizzle of the pair
+        // Z(t + 16 a) sits at (t ^ (s & 15)) + 16 (a ^ (s >> 4))
+        const uint32_t *ze = zp + (t ^ (s & 15)) + 16 * (s >> 4);  // even a
+        const uint32_t *zo = zp + (t ^ (s & 15)) - 16 * (s >> 4);  // odd a
+        float2 x[32];
+#pragma unroll
+        for (int aa = 0; aa < 32; ++aa) x[aa] = unpack_bf2((aa & 1 ? zo : ze)[16 * aa]);
+        reg_fft<32, +1>(x);
+#pragma unroll
+        for (int k = 1; k < 32; ++k) x[k] = cmul(x[k], tw[k * 16 + t]);
+        __syncwarp();  // every spectrum word of both pairs has been read
+        uint32_t *rowp = zp + 32 * t;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) rowp[k ^ lane] = pack_bf2(x[k].x, x[k].y);
+        __syncwarp();
+        float2 y[2][16];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const int lk = lane ^ (16 * kk);  // column k = t + 16 kk of row tt sits at word k ^ tt ^ 16 hw
+#pragma unroll
+          for (int tt = 0; tt < 16; ++tt) y[kk][tt] = unpack_bf2(zp[32 * tt + (lk ^ tt)]);
+          reg_fft<16, +1>(y[kk]);  // y[kk][jj] = c(t + 16 kk + 32 jj)
+        }
+        float vu = -INFINITY, vm = -INFINITY;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            vu = fmaxf(vu, y[kk][jj].x);
+            vm = fmaxf(vm, y[kk][jj].y);
+          }
+        // maxima over the half-warp: threads t < 8 end with max(vu), t >= 8 with max(vm)
+        const bool hi8 = (t & 8) != 0;
+        float v = fmaxf(hi8 ? vm : vu, __shfl_xor_sync(0xffffffffu, hi8 ? vu : vm, 8));
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        const bool valid = rt * 8 + i < a.rows;
+        const int2 ri = rinfo[i];
+        const int64_t rbase = (static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y;
+        if (valid && (t & 7) == 0) a.rowmax[rbase * 2 + (t >> 3)] = (hi8 && !g.mirror) ? -INFINITY : v;
+        if (a.dbg_cc && valid) {
+          float *d = a.dbg_cc + rbase * 2 * M;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = t + 16 * kk + 32 * jj;
+              d[j] = y[kk][jj].x;
+              d[M + ((j + M / 2) & (M - 1))] = y[kk][jj].y;
+            }
+        }
+      }
+    }
+    __syncthreads();  // the next tile's contraction overwrites the pair buffers
+  }
+}
+
 template <int M, int KT, bool FP16>
 __global__ void __launch_bounds__(TcShape<M, KT>::THREADS) cc_tc_kernel(Geometry g, TcArgs a) {
   using Sh = TcShape<M, KT>;
@@ -636,8 +834,26 @@ static cudaError_t launch_tc256(const Geometry &g, const TcArgs &a, cudaStream_t
   return cudaGetLastError();
 }
 
+template <bool FP16>
+static cudaError_t launch_tc512(const Geometry &g, const TcArgs &a, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(cc_tc512_kernel<FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kTc512Smem));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t row_tiles = (a.rows + kTile - 1) / kTile;
+  if (row_tiles <= 0) return cudaSuccess;
+  if (g.NCH > kTc512MaxChunks) return cudaErrorInvalidValue;
+  cc_tc512_kernel<FP16><<<static_cast<unsigned>(row_tiles), kTc512Threads, kTc512Smem, st>>>(
+      g, a, (a.K + kTile - 1) / kTile);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStream_t st) {
   if (g.M == 256) return fp16 ? launch_tc256<true>(g, a, st) : launch_tc256<false>(g, a, st);
+  if (g.M == 512) return fp16 ? launch_tc512<true>(g, a, st) : launch_tc512<false>(g, a, st);
 #define MRA_TC_CASE(MM, KK) \
   case MM: return fp16 ? launch_tc_t<MM, KK, true>(g, a, st) : launch_tc_t<MM, KK, false>(g, a, st);
   switch (g.M) {
@@ -645,7 +861,6 @@ cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStre
     MRA_TC_CASE(32, 8)
     MRA_TC_CASE(64, 8)
     MRA_TC_CASE(128, 8)
-    MRA_TC_CASE(512, 4)
     default: return cudaErrorInvalidValue;
   }
 #undef MRA_TC_CASE

@@ -392,11 +392,14 @@ int build_tables(mra_handle *h) {
     if ((rc = upload(h, kpos16, &g.kpos16, "16-bit frequency bases"))) return rc;
   }
   {
-    // whole frequencies per staging chunk of the M = 256 kernel, greedily
+    // whole frequencies per staging chunk of the M = 256 / M = 512 kernels, greedily
+    const int cap = g.M == 512 ? mra::kTc512ChunkKs : mra::kTc256ChunkKs;
     std::vector<int> chunk_f(1, 0);
     for (int f = 0; f <= H; ++f) {
       const int start = kso[chunk_f.back()];
-      if (f > chunk_f.back() && kso[f + 1] - start > mra::kTc256ChunkKs) chunk_f.push_back(f);
+      if (f > chunk_f.back() && kso[f + 1] - start > cap) chunk_f.push_back(f);
+      if (g.M == 512 && kso[f + 1] - kso[f] > mra::kTc512MaxKsPerF)
+        return set_err(h, MRA_EINVAL, "more than %d k-steps at frequency %d", mra::kTc512MaxKsPerF, f);
     }
     chunk_f.push_back(H + 1);
     g.NCH = static_cast<int>(chunk_f.size()) - 1;

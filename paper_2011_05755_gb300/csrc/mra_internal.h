@@ -49,13 +49,16 @@ struct Geometry {
   // inverse angular DFT (M = 256): [0, 512) stage-1 A, [512, 1024) stage-2 B,
   // each [32 lanes][16 words].
   const uint32_t *dft16;
-  // Staging chunks of the M = 256 tensor-core kernel: chunk c holds the whole
-  // frequencies [chunk_f[c], chunk_f[c + 1]), at most kTc256ChunkKs k-steps.
+  // Staging chunks of the M = 256 and M = 512 tensor-core kernels: chunk c
+  // holds the whole frequencies [chunk_f[c], chunk_f[c + 1]), at most
+  // kTc256ChunkKs (M = 256) or kTc512ChunkKs (M = 512) k-steps.
   int NCH;
   const int *chunk_f;     // [NCH + 1]
 };
 
 constexpr int kTc256ChunkKs = 22;
+constexpr int kTc512ChunkKs = 44;
+constexpr int kTc512MaxKsPerF = 6;  // rings with N_r <= 512 have r <= 81: at most 6 k-steps of 16 per frequency
 
 struct PolarArgs {
   const float *imgs;   // [n][L][L]
