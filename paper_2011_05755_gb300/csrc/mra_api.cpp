@@ -470,9 +470,10 @@ int ensure_chunk_workspace(mra_handle *h) {
       const size_t budget = size_t(2) << 30;
       chunk = static_cast<int>(budget / per_img);
       if (chunk < 1) chunk = 1;
-      if (chunk > 65536) chunk = 65536;
     }
-    // row tiles of one chunk index the contraction kernels' grid.y (<= 65535)
+    // images of one chunk index the polar kernel's grid.y, its row tiles the
+    // contraction kernels' grid.y (both <= 65535)
+    if (chunk > 65535) chunk = 65535;
     const int64_t max_chunk = (int64_t(65535) * mra::kTile) / S;
     if (chunk > max_chunk) chunk = static_cast<int>(max_chunk < 1 ? 1 : max_chunk);
     h->chunk = chunk;

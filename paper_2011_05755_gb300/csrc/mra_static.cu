@@ -216,6 +216,10 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
                 "this configuration needs at least %zu bytes of scratch for one image; the reserved array holds %zu",
                 fixed + per_img + 4096, kScratchBytes);
   int64_t chunk = static_cast<int64_t>((kScratchBytes - fixed - 4096) / per_img);
+  // images of a chunk index the polar kernel's grid.y and its row tiles the
+  // contraction kernel's grid.y (both <= 65535)
+  if (chunk > 65535) chunk = 65535;
+  if (chunk > int64_t(65535) * mra::kTile / S) chunk = int64_t(65535) * mra::kTile / S;
   while (chunk > 1) {  // leave room for tile padding and alignment
     const int64_t tiles = (chunk * S + mra::kTile - 1) / mra::kTile;
     const size_t need = align256(sizeof(unsigned long long) * chunk) +

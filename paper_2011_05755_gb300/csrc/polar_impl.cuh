@@ -2,8 +2,10 @@
 // coordinates with given shift and apply FFT"; for the references the same
 // with no shift, followed by the ring weights of the Sec. 2 quadrature).
 //
-// One CTA handles R consecutive rows (row = image * rows_per_img + shift).
-// Phase 1 writes the bilinear samples of all rows into shared memory; phase 2
+// A CTA stages one image in shared memory and walks groups of R consecutive
+// rows (row = image * rows_per_img + shift): the groups blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Per group, phase 1 writes the bilinear
+// samples of its rows into shared memory; phase 2
 // gives each warp one (row, ring) job: an in-place N/2-point complex FFT of
 // the ring's real samples packed as z_q = x_{2q} + i x_{2q+1}, then the
 // split into the N/2 + 1 real-input bins X(f), written straight into the
@@ -45,6 +47,13 @@ __device__ __forceinline__ uint32_t pack_qp(float q, float p) {
   }
 }
 
+// Position of word w (k-step w / 16, word w % 16) in a row of the (q, p)
+// planes: the word index inside the k-step is XORed with (k-step & 14), so
+// that the stores of one ring's consecutive frequencies (k-steps 1, 2 or 3
+// apart, same word) fall in different banks.  The XOR keeps word pairs
+// (2j, 2j + 1) adjacent.
+__device__ __forceinline__ int plane_swz(int w) { return w ^ ((w >> 4) & 14); }
+
 // All (ring, row) jobs of one ring-length class [i0, i1) of a CTA: forward
 // FFT of the packed samples, real split, weights, and the spectrum written in
 // the layout the path needs (FP32 tiled, 16-bit q/p words, debug).  s_kpos
@@ -83,7 +92,8 @@ __device__ __forceinline__ int ring_class(const Geometry &g, const PolarArgs &a,
         if constexpr (OUT == kOutF32) {
           if (a.out) a.out[((row >> 3) * g.NB + s_kpos[k] + ring) * kTile + (row & 7)] = X;
         } else {
-          planes[i * NB16 + s_kpos[k] + ring] = pack_qp<OUT>(X.x - X.y, X.x + X.y);
+          const int w = s_kpos[k] + ring;  // k-step w / 16, word w % 16 of it
+          planes[i * NB16 + plane_swz(w)] = pack_qp<OUT>(X.x - X.y, X.x + X.y);
         }
       }
     }
@@ -106,15 +116,13 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs
   const int NSp = sample_stride(NS);
   const int LL = L * L;
   const int64_t img = blockIdx.y;
-  const int s0 = blockIdx.x * R;                       // first shift of this CTA
-  const int nrows = min(R, a.rows_per_img - s0);
-  const int64_t row0 = img * a.rows_per_img + s0;
   float *im = reinterpret_cast<float *>(smem_f4);       // the image (with its zero border if TAPS)
   float2 *tws = reinterpret_cast<float2 *>(im + image_floats(g, TAPS));  // [M] forward twiddles
   int *s_kpos = reinterpret_cast<int *>(tws + M);       // [M/2 + 1] output bases (padded to even)
   float *smem = reinterpret_cast<float *>(s_kpos + ((M / 2 + 2) & ~1));  // [R][NSp] samples, then ring FFTs
   const float c0 = 0.5f * static_cast<float>(L);
-  // 16-bit paths: (q, p) words [row][NB16] after the samples (zero = padding)
+  // 16-bit paths: (q, p) words [row][NB16] after the samples; the padding
+  // words are zeroed once, every group rewrites the same non-padding words
   const int NB16 = g.KS * 16;
   uint32_t *planes = reinterpret_cast<uint32_t *>(smem + R * NSp);
   if constexpr (OUT != kOutF32)
@@ -155,100 +163,123 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs
   for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = g.fwd_tw[i];
   __syncthreads();
 
-  // Phase 1: samples x_r(theta_q) = I(c0 + s + r (cos theta_q, sin theta_q)).
-  if constexpr (TAPS) {
-    // integer shifts: the bilinear weights of a sample do not depend on the
-    // shift, which only moves the neighbourhood inside the bordered image
-    const int Lp = L + 2 * g.pad;
-    int soff[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      soff[i] = 0;
-      if (a.use_shifts && i < nrows) {
-        const float2 sh = g.shifts[s0 + i];
-        soff[i] = static_cast<int>(sh.y) * Lp + static_cast<int>(sh.x);
-      }
-    }
-    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
-      const float4 tp = __ldg(g.taps + q);
-      const int base = __float_as_int(tp.x);
-      const float fx = tp.y, fy = tp.z, gx = 1.f - fx, gy = 1.f - fy;
+  for (int s0 = blockIdx.x * R; s0 < a.rows_per_img; s0 += gridDim.x * R) {
+    const int nrows = min(R, a.rows_per_img - s0);
+    const int64_t row0 = img * a.rows_per_img + s0;
+    // Phase 1: samples x_r(theta_q) = I(c0 + s + r (cos theta_q, sin theta_q)).
+    if constexpr (TAPS) {
+      // integer shifts: the bilinear weights of a sample do not depend on the
+      // shift, which only moves the neighbourhood inside the bordered image
+      const int Lp = L + 2 * g.pad;
+      int soff[R];
 #pragma unroll
       for (int i = 0; i < R; ++i) {
-        if (i < nrows) {
-          const float *p = im + base + soff[i];
-          const float v = gy * (gx * p[0] + fx * p[1]) + fy * (gx * p[Lp] + fx * p[Lp + 1]);
-          smem[i * NSp + q] = v;
-          if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+        soff[i] = 0;
+        if (a.use_shifts && i < nrows) {
+          const float2 sh = g.shifts[s0 + i];
+          soff[i] = static_cast<int>(sh.y) * Lp + static_cast<int>(sh.x);
+        }
+      }
+      // eight samples per thread and pass, their tap loads issued together
+      constexpr int QU = 8;
+      for (int q0 = threadIdx.x; q0 < NS; q0 += QU * blockDim.x) {
+        float4 tp[QU];
+#pragma unroll
+        for (int u = 0; u < QU; ++u) {
+          const int q = q0 + u * blockDim.x;
+          tp[u] = q < NS ? __ldg(g.taps + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < QU; ++u) {
+          const int q = q0 + u * blockDim.x;
+          if (q < NS) {
+            const int base = __float_as_int(tp[u].x);
+            const float fx = tp[u].y, fy = tp[u].z, gx = 1.f - fx, gy = 1.f - fy;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              if (i < nrows) {
+                const float *p = im + base + soff[i];
+                const float v = gy * (gx * p[0] + fx * p[1]) + fy * (gx * p[Lp] + fx * p[Lp + 1]);
+                smem[i * NSp + q] = v;
+                if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+              }
+            }
+          }
+        }
+      }
+    } else {
+      float cx[R], cy[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        cx[i] = c0;
+        cy[i] = c0;
+        if (a.use_shifts && i < nrows) {
+          const float2 sh = g.shifts[s0 + i];
+          cx[i] += sh.x;
+          cy[i] += sh.y;
+        }
+      }
+      for (int q = threadIdx.x; q < NS; q += blockDim.x) {
+        const float2 o = g.offs[q];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (i < nrows) {
+            const float v = bilinear_smem(im, L, cx[i] + o.x, cy[i] + o.y);
+            smem[i * NSp + q] = v;
+            if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
+          }
         }
       }
     }
-  } else {
-    float cx[R], cy[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      cx[i] = c0;
-      cy[i] = c0;
-      if (a.use_shifts && i < nrows) {
-        const float2 sh = g.shifts[s0 + i];
-        cx[i] += sh.x;
-        cy[i] += sh.y;
-      }
-    }
-    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
-      const float2 o = g.offs[q];
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        if (i < nrows) {
-          const float v = bilinear_smem(im, L, cx[i] + o.x, cy[i] + o.y);
-          smem[i * NSp + q] = v;
-          if (a.dbg_samples) a.dbg_samples[(row0 + i) * NS + q] = v;
-        }
-      }
-    }
-  }
-  __syncthreads();
-
-  // Phase 2: ring FFTs.  Rings of equal length form a contiguous class; the
-  // (ring, row) jobs of a class are spread over the warps, 32 / T jobs per
-  // warp, each transformed by a group of T threads (group_fft).
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  int fw = 0;  // warp that takes the first pass of the next class
-  for (int i1 = g.NR; i1 > 0;) {
-    const int H = g.rings[i1 - 1].x >> 1;
-    int i0 = i1 - 1;
-    while (i0 > 0 && (g.rings[i0 - 1].x >> 1) == H) --i0;
-#define MRA_RING_CLASS(HH) \
-  fw = ring_class<HH, R, OUT>(g, a, smem, planes, NB16, tws, s_kpos, i0, i1, nrows, row0, warp, lane, nwarps, fw)
-    switch (H) {
-      case 4: MRA_RING_CLASS(4); break;
-      case 8: MRA_RING_CLASS(8); break;
-      case 16: MRA_RING_CLASS(16); break;
-      case 32: MRA_RING_CLASS(32); break;
-      case 64: MRA_RING_CLASS(64); break;
-      case 128: MRA_RING_CLASS(128); break;
-      default: MRA_RING_CLASS(256); break;
-    }
-#undef MRA_RING_CLASS
-    i1 = i0;
-  }
-
-  // Phase 3 (16-bit paths): fragment-order copy-out, 16 bytes per lane slot.
-  if constexpr (OUT != kOutF32) {
     __syncthreads();
-    const int per_k = nrows * 4;
-    for (int idx = threadIdx.x; idx < g.KS * per_k; idx += blockDim.x) {
-      const int kk = idx / per_k;
-      const int rem = idx - kk * per_k;
-      const int i = rem >> 2, t = rem & 3;
-      const int64_t row = row0 + i;
-      const int lane16 = 4 * static_cast<int>(row & 7) + t;
-      const uint32_t *w = planes + i * NB16 + kk * 16 + 2 * t;
-      const uint32_t w0 = w[0], w1 = w[1], w8 = w[8], w9 = w[9];
-      // {q[2t], q[2t+1]}, {p[2t], p[2t+1]}, {q[2t+8], q[2t+9]}, {p[2t+8], p[2t+9]}
-      a.out16[((row >> 3) * g.KS + kk) * 32 + lane16] =
-          make_uint4(__byte_perm(w0, w1, 0x5410), __byte_perm(w0, w1, 0x7632), __byte_perm(w8, w9, 0x5410),
-                     __byte_perm(w8, w9, 0x7632));
+
+    // Phase 2: ring FFTs.  Rings of equal length form a contiguous class; the
+    // (ring, row) jobs of a class are spread over the warps, 32 / T jobs per
+    // warp, each transformed by a group of T threads (group_fft).
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    int fw = 0;  // warp that takes the first pass of the next class
+    for (int i1 = g.NR; i1 > 0;) {
+      const int H = g.rings[i1 - 1].x >> 1;
+      int i0 = i1 - 1;
+      while (i0 > 0 && (g.rings[i0 - 1].x >> 1) == H) --i0;
+#define MRA_RING_CLASS(HH) \
+    fw = ring_class<HH, R, OUT>(g, a, smem, planes, NB16, tws, s_kpos, i0, i1, nrows, row0, warp, lane, nwarps, fw)
+      switch (H) {
+        case 4: MRA_RING_CLASS(4); break;
+        case 8: MRA_RING_CLASS(8); break;
+        case 16: MRA_RING_CLASS(16); break;
+        case 32: MRA_RING_CLASS(32); break;
+        case 64: MRA_RING_CLASS(64); break;
+        case 128: MRA_RING_CLASS(128); break;
+        default: MRA_RING_CLASS(256); break;
+      }
+#undef MRA_RING_CLASS
+      i1 = i0;
+    }
+
+    // Phase 3 (16-bit paths): fragment-order copy-out, 16 bytes per lane slot.
+    if constexpr (OUT != kOutF32) {
+      __syncthreads();
+      const int per_k = nrows * 4;
+      for (int idx = threadIdx.x; idx < g.KS * per_k; idx += blockDim.x) {
+        const int kk = idx / per_k;
+        const int rem = idx - kk * per_k;
+        const int i = rem >> 2, t = rem & 3;
+        const int64_t row = row0 + i;
+        const int lane16 = 4 * static_cast<int>(row & 7) + t;
+        const uint32_t *w = planes + i * NB16 + kk * 16;
+        const uint2 w01 = *reinterpret_cast<const uint2 *>(w + ((2 * t) ^ (kk & 14)));
+        const uint2 w89 = *reinterpret_cast<const uint2 *>(w + ((2 * t + 8) ^ (kk & 14)));
+        const uint32_t w0 = w01.x, w1 = w01.y, w8 = w89.x, w9 = w89.y;
+        // {q[2t], q[2t+1]}, {p[2t], p[2t+1]}, {q[2t+8], q[2t+9]}, {p[2t+8], p[2t+9]}
+        a.out16[((row >> 3) * g.KS + kk) * 32 + lane16] =
+            make_uint4(__byte_perm(w0, w1, 0x5410), __byte_perm(w0, w1, 0x7632), __byte_perm(w8, w9, 0x5410),
+                       __byte_perm(w8, w9, 0x7632));
+      }
+      // the next group's phase 2 rewrites the planes only after the barrier
+      // that follows its phase 1
+    } else {
+      __syncthreads();  // the next group's phase 1 overwrites the samples
     }
   }
 }
@@ -262,7 +293,20 @@ static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t 
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  dim3 grid((a.rows_per_img + R - 1) / R, static_cast<unsigned>(a.n_imgs));
+  // CTAs per image: one (every shift group of the image in one CTA, the image
+  // staged once) unless the images are too few for about four waves of two
+  // CTAs per SM
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t groups = (a.rows_per_img + R - 1) / R;
+  const int64_t want = (static_cast<int64_t>(8) * sms + a.n_imgs - 1) / a.n_imgs;
+  const int per_img = static_cast<int>(want < 1 ? 1 : (want > groups ? groups : want));
+  dim3 grid(static_cast<unsigned>(per_img), static_cast<unsigned>(a.n_imgs));
   polar_fft_kernel<R, TAPS, OUT><<<grid, 256, smem, st>>>(g, a);
   return cudaGetLastError();
 }
