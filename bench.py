@@ -346,7 +346,7 @@ def main():
             cc_line = {"bound": "alu", "kernel": kname + " (FP32 contraction + inverse angular DFT + argmax)",
                        "achieved": flops / cc_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s", "peak_source": alu_src}
         else:
-            kname = "cc_tc256_kernel" if info["M"] == 256 else "cc_tc_kernel"
+            kname = {256: "cc_tc256_kernel", 512: "cc_tc512_kernel"}.get(info["M"], "cc_tc_kernel")
             flops = pairs_per_launch * (f_con + (f_ifft if info["M"] == 256 else 0))
             cc_line = {"bound": "tensor", "kernel": kname + " (16-bit tensor-core contraction"
                        + (" and inverse angular DFT" if info["M"] == 256 else " + FP32 inverse DFT") + ", row maxima)",

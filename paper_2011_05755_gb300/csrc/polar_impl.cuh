@@ -293,9 +293,14 @@ static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t 
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  // CTAs per image: one (every shift group of the image in one CTA, the image
-  // staged once) unless the images are too few for about four waves of two
-  // CTAs per SM
+  // CTAs per image (each walks its share of the image's shift groups and
+  // stages the image once): four when two or more CTAs fit on an SM, so
+  // that the CTAs stay short and the last wave small; one when a CTA fills
+  // an SM, where the image staging would not overlap other work; more when
+  // the images are too few for about four waves of two CTAs per SM.
+  // (Measured on GB300: L = 76, 2 CTAs per SM: 1 / 2 / 4 per image 22.8 /
+  // 21.4 / 20.7 ms per 8192 images; L = 128, 1 CTA per SM: 1 / 2 per image
+  // 51.7 / 57.3 ms per 2048 images.)
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -305,7 +310,9 @@ static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t 
   }
   const int64_t groups = (a.rows_per_img + R - 1) / R;
   const int64_t want = (static_cast<int64_t>(8) * sms + a.n_imgs - 1) / a.n_imgs;
-  const int per_img = static_cast<int>(want < 1 ? 1 : (want > groups ? groups : want));
+  int64_t per_img = smem + 1024 <= 232448 / 2 ? 4 : 1;
+  if (per_img < want) per_img = want;
+  if (per_img > groups) per_img = groups;
   dim3 grid(static_cast<unsigned>(per_img), static_cast<unsigned>(a.n_imgs));
   polar_fft_kernel<R, TAPS, OUT><<<grid, 256, smem, st>>>(g, a);
   return cudaGetLastError();
