@@ -249,6 +249,18 @@ static cudaError_t launch_cc_t(const Geometry &g, const CCArgs &a, cudaStream_t 
   return cudaGetLastError();
 }
 
+size_t cc_fp32_smem(int M, int seg_max) {
+  switch (M) {
+    case 16: return CCShape<16, 8>::smem(seg_max);
+    case 32: return CCShape<32, 8>::smem(seg_max);
+    case 64: return CCShape<64, 8>::smem(seg_max);
+    case 128: return CCShape<128, 8>::smem(seg_max);
+    case 256: return CCShape<256, 8>::smem(seg_max);
+    case 512: return CCShape<512, 4>::smem(seg_max);
+    default: return 0;
+  }
+}
+
 cudaError_t launch_cc_fp32(const Geometry &g, const CCArgs &a, cudaStream_t st) {
   switch (g.M) {
     case 16: return launch_cc_t<16, 8>(g, a, st);

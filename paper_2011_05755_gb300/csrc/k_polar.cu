@@ -7,6 +7,10 @@ namespace mra {
 
 cudaError_t launch_polar16(const Geometry &g, const PolarArgs &a, cudaStream_t st);
 
+size_t polar_smem_one_row(const Geometry &g, bool taps, bool out16) {
+  return polar_smem_bytes(g, taps, out16, 1);
+}
+
 cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
   if (a.n_imgs <= 0 || a.rows_per_img <= 0) return cudaSuccess;
   if (a.out16) return launch_polar16(g, a, st);

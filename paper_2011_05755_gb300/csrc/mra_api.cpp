@@ -194,6 +194,66 @@ int upload(mra_handle *h, const std::vector<T> &v, const T **out, const char *wh
   return MRA_OK;
 }
 
+// Whether every kernel the configuration launches fits the per-CTA shared
+// memory limit (host arithmetic only, before any CUDA call).  The sizes
+// follow the table construction in build_tables; the staged image is
+// counted with the widest zero border (8 pixels) whenever the shift grid is
+// integral.  MRA_EUNSUPPORTED names the kernel that does not fit.
+int fits_shared_memory(const mra_config_t &c, std::string *why) {
+  std::vector<int> NN;
+  for (int r = c.first_ring; r <= c.last_ring; r += c.ring_step) {
+    int n = 1;
+    while (n < kTwoPi * r) n *= 2;
+    NN.push_back(n);
+  }
+  int M = 0;
+  for (int n : NN) M = n > M ? n : M;
+  if (M < 16 || M > 512) return MRA_OK;  // reported by build_tables
+  mra::Geometry g{};
+  g.L = c.L;
+  g.M = M;
+  g.NR = static_cast<int>(NN.size());
+  for (int n : NN) {
+    g.NS += n;
+    g.NBIN += n / 2 + 1;
+  }
+  int seg_max = 0;
+  for (int f = 0; f <= M / 2; ++f) {
+    int R = 0;
+    for (int n : NN) R += n / 2 >= f;
+    g.KS += (R + 15) / 16;
+    seg_max = std::max(seg_max, (R + 1) & ~1);
+  }
+  const double nx = std::round(2.0 * double(c.shift_range) / double(c.shift_step)) + 1.0;
+  bool integral = true;
+  for (int i = 0; i < static_cast<int>(nx); ++i) {
+    const float v = -c.shift_range + static_cast<float>(i) * c.shift_step;
+    integral = integral && v == std::floor(v);
+  }
+  g.pad = 8;
+  const bool half = c.precision != MRA_FP32;
+  struct Need {
+    const char *kernel;
+    size_t bytes;
+  };
+  std::vector<Need> needs = {{"polar resampling / ring FFT", mra::polar_smem_one_row(g, integral, half)}};
+  if (half)
+    needs.push_back({"FP32 rescore", mra::rescore_smem(g)});
+  else
+    needs.push_back({"FP32 contraction", mra::cc_fp32_smem(M, seg_max)});
+  for (const Need &n : needs)
+    if (n.bytes > mra::kMaxSmemPerBlock) {
+      char buf[256];
+      std::snprintf(buf, sizeof(buf),
+                    "the %s kernel would need %zu bytes of shared memory per CTA for this configuration; at most "
+                    "%zu are available (smaller box, fewer rings, or MRA_FP32)",
+                    n.kernel, n.bytes, mra::kMaxSmemPerBlock);
+      *why = buf;
+      return MRA_EUNSUPPORTED;
+    }
+  return MRA_OK;
+}
+
 int validate(const mra_config_t *c, std::string *why) {
   char buf[256];
   auto bad = [&](const char *m) {
@@ -219,7 +279,7 @@ int validate(const mra_config_t *c, std::string *why) {
   if (c->precision != MRA_FP32 && c->precision != MRA_BF16_RESCORE && c->precision != MRA_FP16_RESCORE)
     return bad("precision must be MRA_FP32, MRA_BF16_RESCORE or MRA_FP16_RESCORE");
   if (c->chunk_images < 0) return bad("chunk_images must be >= 0");
-  return MRA_OK;
+  return fits_shared_memory(*c, why);
 }
 
 // Build every geometry table of the configuration (FP64 on the host).
@@ -718,7 +778,7 @@ int mra_create(const mra_config_t *cfg, mra_t *out) {
   if (!out) return set_err(nullptr, MRA_EINVAL, "out is NULL");
   *out = nullptr;
   std::string why;
-  if (validate(cfg, &why)) return set_err(nullptr, MRA_EINVAL, "%s", why.c_str());
+  if (int rc = validate(cfg, &why)) return set_err(nullptr, rc, "%s", why.c_str());
   auto *h = new mra_handle();
   h->cfg = *cfg;
   cudaError_t e = cudaGetDevice(&h->device);

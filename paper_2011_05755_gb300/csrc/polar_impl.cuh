@@ -318,15 +318,23 @@ static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t 
   return cudaGetLastError();
 }
 
-template <bool TAPS, int OUT>
-static cudaError_t launch_polar_t(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
-  const size_t fixed = static_cast<size_t>(image_floats(g, TAPS)) * sizeof(float) + g.M * sizeof(float2) +
+// Shared memory of a CTA with R rows: the staged image, the twiddles, the
+// output bases, then per row the samples and (16-bit output) the planes.
+inline size_t polar_smem_bytes(const Geometry &g, bool taps, bool out16, int R) {
+  const size_t fixed = static_cast<size_t>(image_floats(g, taps)) * sizeof(float) + g.M * sizeof(float2) +
                        static_cast<size_t>((g.M / 2 + 2) & ~1) * sizeof(int);
   size_t per_row = static_cast<size_t>(sample_stride(g.NS)) * sizeof(float);
-  if (OUT != kOutF32) per_row += static_cast<size_t>(g.KS) * 16 * sizeof(uint32_t);
+  if (out16) per_row += static_cast<size_t>(g.KS) * 16 * sizeof(uint32_t);
+  return fixed + per_row * R;
+}
+
+template <bool TAPS, int OUT>
+static cudaError_t launch_polar_t(const Geometry &g, const PolarArgs &a, cudaStream_t st) {
+  const size_t fixed = polar_smem_bytes(g, TAPS, OUT != kOutF32, 0);
+  const size_t per_row = polar_smem_bytes(g, TAPS, OUT != kOutF32, 1) - fixed;
   // two CTAs per SM when the rows fit in ~110 KB, else as many rows as fit in 200 KB
   int R = static_cast<int>((112640 > fixed ? 112640 - fixed : 0) / per_row);
-  if (R < 1) R = static_cast<int>((204800 - fixed) / per_row);
+  if (R < 1) R = static_cast<int>((204800 > fixed ? 204800 - fixed : 0) / per_row);
   R = R < 1 ? 1 : (R > 4 ? 4 : R);
   if (R > a.rows_per_img) R = a.rows_per_img;
   const size_t smem = fixed + per_row * R;
