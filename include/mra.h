@@ -111,7 +111,14 @@ typedef struct {
 } mra_info_t;
 
 /* Create a handle for one configuration.  Host-synchronous; allocates the
- * geometry tables on the current device.  *out is set only on MRA_OK. */
+ * geometry tables on the current device.  *out is set only on MRA_OK.
+ * Errors: MRA_EINVAL for a malformed configuration (see mra_config_t);
+ * MRA_EUNSUPPORTED, before any CUDA call, when a kernel the configuration
+ * launches would need more than 227 KB of shared memory per CTA (the
+ * message names it; e.g. the 16-bit paths' FP32 rescore CTA holds one
+ * image, its ring samples and its ring spectra, which exceeds the limit
+ * from about L = 130 with rings beyond 62); MRA_ECUDA if a CUDA call
+ * fails. */
 int mra_create(const mra_config_t *cfg, mra_t *out);
 
 /* Release the handle and all device memory it owns (synchronises the device
