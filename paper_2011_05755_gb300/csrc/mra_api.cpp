@@ -227,7 +227,7 @@ int fits_shared_memory(const mra_config_t &c, std::string *why) {
   const double nx = std::round(2.0 * double(c.shift_range) / double(c.shift_step)) + 1.0;
   bool integral = true;
   for (int i = 0; i < static_cast<int>(nx); ++i) {
-    const float v = -c.shift_range + static_cast<float>(i) * c.shift_step;
+    const float v = static_cast<float>(-double(c.shift_range) + i * double(c.shift_step));  // as build_tables
     integral = integral && v == std::floor(v);
   }
   g.pad = 8;
