@@ -85,8 +85,8 @@ typedef struct {
     int32_t chunk_images;
 } mra_config_t;
 
-/* Per-image result (Algorithm 1: "find the corresponding alignment
- * parameters").  32 bytes, naturally aligned. */
+/* Per-image result (Alg. 1, parameter-lookup step: the alignment
+ * parameters of the best CC value).  32 bytes, naturally aligned. */
 typedef struct {
     int32_t k;          /* best reference (class)                          */
     int32_t ang_idx;    /* j: angle phi_j = 2 pi j / M                       */
@@ -131,7 +131,8 @@ const char *mra_last_error(mra_t h);
 
 int mra_get_info(mra_t h, mra_info_t *info);
 
-/* Algorithm 1, "convert y_i to polar coordinates and apply FFT": resample
+/* Alg. 1, reference-preparation step (polar conversion and FFT of every
+ * reference before the particle loop): resample
  * the K references d_refs [K][L][L] (float32, device) on the rings with no
  * shift, take each ring's real DFT, scale bin f of ring r by
  * 2 pi r dr / N_r^2 (halved at f = N_r/2 when N_r < M) and keep the result
@@ -159,7 +160,8 @@ int mra_copy_refs(mra_t dst, mra_t src, mra_stream_t stream);
 int mra_align(mra_t h, const float *d_imgs, int64_t n, mra_pose_t *d_poses,
               mra_stream_t stream);
 
-/* Algorithm 1, "compute new Y' from aligned images": for every class k,
+/* Alg. 1, class-average step (new references Y' from the aligned
+ * particles): for every class k,
  * avg_k = (1/n_k) sum_{i: k_i = k} a_i with a_i(c0 + w) = I_i(c0 + s_i +
  * Mm_i R(-phi_i) w) on the integer grid (bilinear, zero outside), summed in
  * FP32 with Neumaier compensation in a fixed order (deterministic).
@@ -233,30 +235,39 @@ int mra_profile_read(mra_t h, mra_stage_time_t *out);
 
 /* ---- Alignment without device allocation ----
  * (No counterpart in the paper: this serves callers rather than the method.)
- * For code that may not call cudaMalloc at all — a framework that owns every
+ * For code that may not call cudaMalloc at all: a framework that owns every
  * device allocation through its own pool, a latency-critical loop where an
  * allocation could stall or fail, a process whose free device memory is
  * promised elsewhere.  Such a caller cannot create a handle (mra_create
  * allocates), so this call takes the configuration directly and runs the
  * FP32 alignment of mra_align (precision must be MRA_FP32) with every
- * intermediate — geometry tables, reference spectra, one chunk of particle
- * spectra, argmax keys — inside one fixed device array of
- * MRA_STATIC_SCRATCH_BYTES that the library reserves on each GPU when it is
- * loaded and keeps until the process exits.  It calls no allocating routine.
+ * intermediate (geometry tables, reference spectra, one chunk of particle
+ * spectra, argmax keys) inside one fixed device array of
+ * MRA_STATIC_SCRATCH_BYTES, a file-scope __device__ array of the library.
+ * It calls no allocating routine.
  *   d_refs [K][L][L], d_imgs [n][L][L] float32 and d_poses [n] are the
  *   caller's device buffers (same meaning as mra_set_refs / mra_align);
  *   msg (may be NULL) receives an error text of at most msg_len bytes.
- *   Images are processed in chunks that fit the array; a configuration whose
- *   tables and reference spectra plus one image do not fit is rejected with
- *   MRA_EINVAL and a message giving the bytes it would need.
- *   The first call on a device, with that device current, looks up the
- *   array's device address (cudaGetSymbolAddress); make that first call
- *   before any stream capture.
- *   Host-synchronous (returns after the poses are written; MRA_ETIMEOUT if a
+ *   The configuration gets every check of mra_create (MRA_EINVAL,
+ *   MRA_EUNSUPPORTED) before any CUDA call.  Images are processed in chunks
+ *   that fit the array; a configuration whose tables and reference spectra
+ *   plus one image (its rows padded to whole tiles) do not fit is rejected
+ *   with MRA_EINVAL and a message giving the bytes it would need.
+ *   With CUDA's default lazy module loading the array is committed on a
+ *   device at the first use there: the first call on each device, with that
+ *   device current, looks up the array's device address
+ *   (cudaGetSymbolAddress), and that first call can return MRA_ECUDA (out of
+ *   memory) if the device has no room for the array.  The first call on
+ *   each device should come before any stream capture.  Once committed, the
+ *   array stays until the process exits.
+ *   Host-synchronous: before returning, the call synchronises `stream` and
+ *   reads a device failure flag with a blocking copy (MRA_ETIMEOUT if a
  *   kernel gave up a bounded wait).  Every call uses the same array, which
  *   keeps the previous call's contents (each call clears what must start at
- *   zero); calls whose GPU work overlaps — from two host threads or on two
- *   streams — race on it and give wrong results. */
+ *   zero).  Calls whose GPU work overlapped would race on the array; the
+ *   library prevents that with a process-wide lock held from the first
+ *   enqueue until the call's GPU work has finished (also on error returns),
+ *   so calls from several host threads run one after another. */
 #define MRA_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, const float *d_imgs, int64_t n,
                      mra_pose_t *d_poses, mra_stream_t stream, char *msg, int32_t msg_len);

@@ -117,7 +117,8 @@ def ring_weights(rings: Sequence[tuple], ring_step: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Polar conversion (Algorithm 1: "convert to polar coordinates (with given shift)")
+# Polar conversion (Alg. 1, shift-loop conversion step: resampling on the rings
+# about the shifted centre)
 # ---------------------------------------------------------------------------
 
 def bilinear(img: np.ndarray, x: np.ndarray, y: np.ndarray) -> np.ndarray:

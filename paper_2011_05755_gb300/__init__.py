@@ -136,6 +136,17 @@ def _dev_ptr(t: torch.Tensor, dtype, name: str) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _check_stack(t: torch.Tensor, L: int, name: str) -> None:
+    """A stack of L x L images: [n, L, L] (checked before any pointer reaches the library)."""
+    if t.dim() != 3 or tuple(t.shape[1:]) != (L, L):
+        raise ValueError(f"{name} must have shape [n, {L}, {L}], got {list(t.shape)}")
+
+
+def _check_poses(p: torch.Tensor, n: int, name: str = "poses") -> None:
+    if p.dim() != 2 or tuple(p.shape) != (n, 8):
+        raise ValueError(f"{name} must have shape [{n}, 8] (mra_pose_t rows), got {list(p.shape)}")
+
+
 def _host_ptr(a, dtype, name: str):
     if isinstance(a, torch.Tensor):
         if a.is_cuda or a.dtype != dtype or not a.is_contiguous():
@@ -181,8 +192,11 @@ def mra_copy_refs(dst, src, stream=None) -> None:
 def mra_align(h, imgs: torch.Tensor, poses: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """Returns poses as an int32 tensor [n, 8] in mra_pose_t layout (see :func:`decode_poses`)."""
     n = imgs.shape[0]
+    if imgs.dim() != 3 or imgs.shape[1] != imgs.shape[2]:
+        raise ValueError(f"imgs must have shape [n, L, L], got {list(imgs.shape)}")
     if poses is None:
         poses = torch.empty((n, 8), dtype=torch.int32, device=imgs.device)
+    _check_poses(poses, n)
     _check(load_library().mra_align(h, _dev_ptr(imgs, torch.float32, "imgs"), n,
                                     _dev_ptr(poses, torch.int32, "poses"), _stream(stream)), h)
     return poses
@@ -257,6 +271,9 @@ def mra_align_static(refs: torch.Tensor, imgs: torch.Tensor, poses: torch.Tensor
                      last_ring: int, ring_step: int = 1, shift_range: float = 0.0, shift_step: float = 1.0,
                      mirror: int = 1, stream=None) -> None:
     """FP32 alignment that allocates no device memory (no handle); see include/mra.h."""
+    _check_stack(refs, L, "refs")
+    _check_stack(imgs, L, "imgs")
+    _check_poses(poses, imgs.shape[0])
     cfg = MRAConfig(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, MRA_FP32, 0)
     buf = ctypes.create_string_buffer(512)
     rc = load_library().mra_align_static(ctypes.byref(cfg), _dev_ptr(refs, torch.float32, "refs"), refs.shape[0],
@@ -314,6 +331,7 @@ class Aligner:
         return mra_get_info(self.h)
 
     def set_refs(self, refs: torch.Tensor, stream=None):
+        _check_stack(refs, self.L, "refs")
         mra_set_refs(self.h, refs, stream)
         self.K = refs.shape[0]
 
@@ -322,9 +340,20 @@ class Aligner:
         self.K = other.K
 
     def align(self, imgs: torch.Tensor, poses=None, stream=None) -> torch.Tensor:
+        _check_stack(imgs, self.L, "imgs")
+        if poses is not None:
+            _check_poses(poses, imgs.shape[0])
         return mra_align(self.h, imgs, poses, stream)
 
     def average(self, imgs, poses, avg=None, counts=None, stream=None):
+        _check_stack(imgs, self.L, "imgs")
+        _check_poses(poses, imgs.shape[0])
+        if avg is not None:
+            _check_stack(avg, self.L, "avg")
+            if avg.shape[0] != self.K:
+                raise ValueError(f"avg must hold K = {self.K} classes, got {avg.shape[0]}")
+        if counts is not None and tuple(counts.shape) != (self.K,):
+            raise ValueError(f"counts must have shape [{self.K}], got {list(counts.shape)}")
         if avg is None:
             avg = torch.zeros((self.K, self.L, self.L), dtype=torch.float32, device=imgs.device)
         if counts is None:
@@ -333,16 +362,19 @@ class Aligner:
         return avg, counts
 
     def debug_polar(self, imgs, stream=None):
+        _check_stack(imgs, self.L, "imgs")
         i = self.info
         out = torch.empty((imgs.shape[0], i["S"], i["n_samples"]), dtype=torch.float32, device=imgs.device)
         return mra_debug_polar(self.h, imgs, out, stream)
 
     def debug_spectra(self, imgs, stream=None):
+        _check_stack(imgs, self.L, "imgs")
         i = self.info
         out = torch.empty((imgs.shape[0], i["S"], i["n_bins"], 2), dtype=torch.float32, device=imgs.device)
         return mra_debug_spectra(self.h, imgs, out, stream)
 
     def debug_cc(self, imgs, stream=None):
+        _check_stack(imgs, self.L, "imgs")
         i = self.info
         out = torch.empty((imgs.shape[0], self.K, i["S"], 2, i["M"]), dtype=torch.float32, device=imgs.device)
         return mra_debug_cc(self.h, imgs, out, stream)

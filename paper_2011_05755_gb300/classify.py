@@ -1,6 +1,6 @@
 """Iterative 2D classification by multi-reference alignment.
 
-The outer loop of Algorithm 1 ("repeat until convergence"): align every
+The outer loop of Alg. 1 (its convergence loop): align every
 particle against the current references, rebuild the class averages from
 the aligned images, normalise them (zero mean, unit standard deviation over
 the box) and use them as the next references (Sec. 2 describes the same

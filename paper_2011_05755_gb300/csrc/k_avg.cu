@@ -1,5 +1,5 @@
-// Class averaging (Algorithm 1: "compute new Y' from aligned images"; in
-// the paper this step runs in CuPy, Sec. 3).
+// Class averaging (Alg. 1, class-average step: the new references Y' are
+// built from the aligned particles; the paper runs this step in CuPy, Sec. 3).
 //
 // For class k: avg_k(c0 + w) = (1/n_k) sum_{i: k_i = k} I_i(c0 + s_i + Mm_i R(-phi_i) w)
 // on the integer grid w, bilinear with zero outside the box.

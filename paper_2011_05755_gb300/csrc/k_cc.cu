@@ -1,8 +1,9 @@
 // Fused spectrum contraction, inverse angular FFT and argmax (FP32 path).
 //
-// Algorithm 1, inner loop: "compute CC between x'_i and y'_i and store CC
-// into the table", "apply inverse FFT to CC table", then "find the largest
-// CC value for each image using reduction".  The CC table of Sec. 2 is never
+// Alg. 1, inner loop (CC step, inverse-FFT step, per-image reduction step):
+// the ring spectra of every shifted particle are correlated with every
+// reference, transformed back over the angle, and reduced to the best value
+// per image.  The CC table of Sec. 2 is never
 // materialised: each CTA owns a tile of 8 rows (image, shift) x KT
 // references, holds the per-pair angular spectrum in shared memory, and
 // reduces the correlation over angles on chip.
@@ -273,7 +274,8 @@ cudaError_t launch_cc_fp32(const Geometry &g, const CCArgs &a, cudaStream_t st) 
   }
 }
 
-// Pose decode (Algorithm 1: "find the corresponding alignment parameters").
+// Pose decode (Alg. 1, parameter-lookup step: the argmax index becomes the
+// reference, angle, shift and mirror of the image).
 __global__ void decode_kernel(Geometry g, const unsigned long long *best, int64_t n, int K,
                               mra_pose_t *poses) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;

@@ -194,33 +194,40 @@ int upload(mra_handle *h, const std::vector<T> &v, const T **out, const char *wh
   return MRA_OK;
 }
 
+}  // namespace
+
+namespace mra {
+
 // Whether every kernel the configuration launches fits the per-CTA shared
-// memory limit (host arithmetic only, before any CUDA call).  The sizes
-// follow the table construction in build_tables; the staged image is
-// counted with the widest zero border (8 pixels) whenever the shift grid is
-// integral.  MRA_EUNSUPPORTED names the kernel that does not fit.
-int fits_shared_memory(const mra_config_t &c, std::string *why) {
-  std::vector<int> NN;
-  for (int r = c.first_ring; r <= c.last_ring; r += c.ring_step) {
+// memory limit (host arithmetic only, before any CUDA call; no heap use, so
+// the allocation-free entry point can call it too).  The sizes follow the
+// table construction in build_tables; the staged image is counted with the
+// widest zero border (8 pixels) whenever the shift grid is integral.
+// MRA_EUNSUPPORTED names the kernel that does not fit.  Expects a
+// configuration whose rings give 16 <= M <= 512 (at most 81 rings).
+static int fits_shared_memory(const mra_config_t &c, char *why, size_t why_len) {
+  constexpr int kMaxRingsChecked = 96;
+  int NN[kMaxRingsChecked];
+  int NR = 0;
+  for (int r = c.first_ring; r <= c.last_ring && NR < kMaxRingsChecked; r += c.ring_step) {
     int n = 1;
     while (n < kTwoPi * r) n *= 2;
-    NN.push_back(n);
+    NN[NR++] = n;
   }
   int M = 0;
-  for (int n : NN) M = n > M ? n : M;
-  if (M < 16 || M > 512) return MRA_OK;  // reported by build_tables
-  mra::Geometry g{};
+  for (int i = 0; i < NR; ++i) M = NN[i] > M ? NN[i] : M;
+  Geometry g{};
   g.L = c.L;
   g.M = M;
-  g.NR = static_cast<int>(NN.size());
-  for (int n : NN) {
-    g.NS += n;
-    g.NBIN += n / 2 + 1;
+  g.NR = NR;
+  for (int i = 0; i < NR; ++i) {
+    g.NS += NN[i];
+    g.NBIN += NN[i] / 2 + 1;
   }
   int seg_max = 0;
   for (int f = 0; f <= M / 2; ++f) {
     int R = 0;
-    for (int n : NN) R += n / 2 >= f;
+    for (int i = 0; i < NR; ++i) R += NN[i] / 2 >= f;
     g.KS += (R + 15) / 16;
     seg_max = std::max(seg_max, (R + 1) & ~1);
   }
@@ -236,28 +243,22 @@ int fits_shared_memory(const mra_config_t &c, std::string *why) {
     const char *kernel;
     size_t bytes;
   };
-  std::vector<Need> needs = {{"polar resampling / ring FFT", mra::polar_smem_one_row(g, integral, half)}};
-  if (half)
-    needs.push_back({"FP32 rescore", mra::rescore_smem(g)});
-  else
-    needs.push_back({"FP32 contraction", mra::cc_fp32_smem(M, seg_max)});
+  const Need needs[2] = {{"polar resampling / ring FFT", polar_smem_one_row(g, integral, half)},
+                         half ? Need{"FP32 rescore", rescore_smem(g)} : Need{"FP32 contraction", cc_fp32_smem(M, seg_max)}};
   for (const Need &n : needs)
-    if (n.bytes > mra::kMaxSmemPerBlock) {
-      char buf[256];
-      std::snprintf(buf, sizeof(buf),
+    if (n.bytes > kMaxSmemPerBlock) {
+      std::snprintf(why, why_len,
                     "the %s kernel would need %zu bytes of shared memory per CTA for this configuration; at most "
                     "%zu are available (smaller box, fewer rings, or MRA_FP32)",
-                    n.kernel, n.bytes, mra::kMaxSmemPerBlock);
-      *why = buf;
+                    n.kernel, n.bytes, kMaxSmemPerBlock);
       return MRA_EUNSUPPORTED;
     }
   return MRA_OK;
 }
 
-int validate(const mra_config_t *c, std::string *why) {
-  char buf[256];
+int check_config(const mra_config_t *c, char *why, size_t why_len) {
   auto bad = [&](const char *m) {
-    *why = m;
+    std::snprintf(why, why_len, "%s", m);
     return MRA_EINVAL;
   };
   if (!c) return bad("config is NULL");
@@ -266,20 +267,40 @@ int validate(const mra_config_t *c, std::string *why) {
   if (c->last_ring < c->first_ring) return bad("last_ring must be >= first_ring");
   if (c->ring_step < 1) return bad("ring_step must be >= 1");
   if (!(c->shift_range >= 0.f) || !std::isfinite(c->shift_range)) return bad("shift_range must be finite and >= 0");
-  if (!(c->shift_step > 0.f) || !std::isfinite(c->shift_step)) return bad("shift_step must be > 0");
+  if (!(c->shift_step > 0.f) || !std::isfinite(c->shift_step)) return bad("shift_step must be finite and > 0");
   const double q = 2.0 * double(c->shift_range) / double(c->shift_step);
-  if (std::fabs(q - std::round(q)) > 1e-6) return bad("2*shift_range/shift_step must be an integer");
+  if (!std::isfinite(q) || std::fabs(q - std::round(q)) > 1e-6) return bad("2*shift_range/shift_step must be an integer");
   const double nx = std::round(q) + 1.0;
-  if (nx * nx > 4096.0) {
-    std::snprintf(buf, sizeof(buf), "shift grid has %.0f points; at most 4096 are supported", nx * nx);
-    *why = buf;
+  if (nx * nx > 4096.0) {  // in double: no overflow for any finite grid
+    std::snprintf(why, why_len, "shift grid has %.0f points; at most 4096 are supported", nx * nx);
     return MRA_EINVAL;
   }
   if (c->mirror != 0 && c->mirror != 1) return bad("mirror must be 0 or 1");
   if (c->precision != MRA_FP32 && c->precision != MRA_BF16_RESCORE && c->precision != MRA_FP16_RESCORE)
     return bad("precision must be MRA_FP32, MRA_BF16_RESCORE or MRA_FP16_RESCORE");
   if (c->chunk_images < 0) return bad("chunk_images must be >= 0");
-  return fits_shared_memory(*c, why);
+  // the largest ring sets M = its ring length
+  const long long r_max = c->first_ring + (static_cast<long long>(c->last_ring - c->first_ring) / c->ring_step) *
+                                              c->ring_step;
+  long long M = 1;
+  while (M < kTwoPi * static_cast<double>(r_max) && M <= 1024) M *= 2;
+  if (M < 16 || M > 512) {
+    std::snprintf(why, why_len, "largest ring length M = %lld; supported range is 16..512 (last ring 3..81)", M);
+    return MRA_EINVAL;
+  }
+  return fits_shared_memory(*c, why, why_len);
+}
+
+}  // namespace mra
+
+namespace {
+
+int validate(const mra_config_t *c, std::string *why) {
+  char buf[320];
+  buf[0] = '\0';
+  const int rc = mra::check_config(c, buf, sizeof(buf));
+  *why = buf;
+  return rc;
 }
 
 // Build every geometry table of the configuration (FP64 on the host).

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/mra.h"
+
 namespace mra {
 
 // Rows of the particle-spectrum layout and columns of the reference-spectrum
@@ -119,6 +121,9 @@ size_t rescore_smem(const Geometry &g);
 size_t polar_smem_one_row(const Geometry &g, bool taps, bool out16);
 size_t cc_fp32_smem(int M, int seg_max);
 constexpr size_t kMaxSmemPerBlock = 232448;  // 227 KB
+// Every check mra_create makes on a configuration, without CUDA calls or heap
+// use: MRA_OK, MRA_EINVAL or MRA_EUNSUPPORTED with a message in why.
+int check_config(const mra_config_t *c, char *why, size_t why_len);
 
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_polar(const Geometry &g, const PolarArgs &a, cudaStream_t st);

@@ -2,20 +2,24 @@
 // not allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc is not allowed or not
-// wanted — inside a framework that owns every device allocation through its
+// wanted: inside a framework that owns every device allocation through its
 // own pool, in a real-time loop where an allocation could stall or fail, or
 // in a process that has handed all free device memory to someone else.  Such
 // a caller cannot create an mra_t handle (mra_create allocates its geometry
 // tables and workspaces), so this entry point takes the configuration
-// directly and keeps every intermediate — geometry tables, reference
-// spectra, particle spectra of one chunk, argmax keys — in a single
-// fixed-size device array that the library reserves for each GPU when it is
-// loaded (MRA_STATIC_SCRATCH_BYTES, held until the process exits).
+// directly and keeps every intermediate (geometry tables, reference
+// spectra, particle spectra of one chunk, argmax keys) in a single
+// fixed-size file-scope device array (MRA_STATIC_SCRATCH_BYTES).  Under
+// CUDA's lazy module loading the array is committed on a device by the first
+// call there (its cudaGetSymbolAddress) and then held until the process
+// exits.
 //
 // The array is shared by every call in the process: the last call's data
-// stays in it, whatever must start at zero is cleared by each call, and two
-// calls whose GPU work overlaps (different streams or host threads) corrupt
-// each other.  The kernels are the ones mra_align uses.
+// stays in it and whatever must start at zero is cleared by each call.  Two
+// calls whose GPU work overlapped would corrupt each other, so a call holds
+// a process-wide lock from its first enqueue until its GPU work has finished
+// (error returns after an enqueue synchronise the stream first).  The
+// kernels are the ones mra_align uses.
 #include "../../include/mra.h"
 
 #include <cmath>
@@ -68,6 +72,22 @@ int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+// The same after work has been enqueued on `st`: wait for that work first,
+// so that the next call (which may take the lock as soon as this one drops
+// it) cannot overwrite the array while this call's copies or kernels still
+// use it.
+int fail_sync(cudaStream_t st, int code, const char *fmt, ...) {
+  cudaStreamSynchronize(st);
+  cudaGetLastError();
+  if (g_msg && g_msg_len > 0) {
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_msg, static_cast<size_t>(g_msg_len), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
@@ -81,17 +101,17 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   g_msg = msg;
   g_msg_len = msg_len;
   if (msg && msg_len > 0) msg[0] = '\0';
-  if (!cfg) return fail(MRA_EINVAL, "config is NULL");
+  // The checks of mra_create (shift grid in double with finiteness, ring
+  // range, shared memory per CTA), before any table is built or CUDA call made.
+  {
+    char why[320];
+    why[0] = '\0';
+    if (int rc = mra::check_config(cfg, why, sizeof(why))) return fail(rc, "%s", why);
+  }
   const mra_config_t &c = *cfg;
-  if (c.L < 8 || c.L > 1024 || (c.L & 1)) return fail(MRA_EINVAL, "L must be even and in [8, 1024]");
-  if (c.first_ring < 1 || c.last_ring < c.first_ring || c.ring_step < 1) return fail(MRA_EINVAL, "bad rings");
-  if (!(c.shift_range >= 0.f) || !(c.shift_step > 0.f)) return fail(MRA_EINVAL, "bad shift grid");
   const double qd = 2.0 * double(c.shift_range) / double(c.shift_step);
-  if (std::fabs(qd - std::round(qd)) > 1e-6) return fail(MRA_EINVAL, "2*shift_range/shift_step must be an integer");
-  const int nx = static_cast<int>(std::lround(qd)) + 1;
+  const int nx = static_cast<int>(std::lround(qd)) + 1;  // check_config bounded nx * nx by 4096
   const int S = nx * nx;
-  if (S > kMaxShifts) return fail(MRA_EINVAL, "shift grid has %d points; at most %d", S, kMaxShifts);
-  if (c.mirror != 0 && c.mirror != 1) return fail(MRA_EINVAL, "mirror must be 0 or 1");
   if (c.precision != MRA_FP32) return fail(MRA_EUNSUPPORTED, "mra_align_static runs the FP32 path only");
   if (K < 1) return fail(MRA_EINVAL, "K must be >= 1");
   if (n < 0) return fail(MRA_EINVAL, "n must be >= 0");
@@ -210,34 +230,34 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   const size_t b_bytes = static_cast<size_t>(Kpad) * NB * sizeof(float2);
   float2 *d_B = reinterpret_cast<float2 *>(take(b_bytes));
   const size_t fixed = off;
-  const size_t per_img = static_cast<size_t>(S) * NB * sizeof(float2) + sizeof(unsigned long long);
-  if (fixed + per_img + 4096 > kScratchBytes)
+  // Bytes of the argmax keys and the tiled particle spectra of a chunk of
+  // `ch` images (rows padded to whole tiles of 8, each piece 256-aligned).
+  auto chunk_bytes = [&](int64_t ch) {
+    const int64_t tiles = (ch * S + mra::kTile - 1) / mra::kTile;
+    return align256(sizeof(unsigned long long) * ch) + static_cast<size_t>(tiles) * NB * mra::kTile * sizeof(float2);
+  };
+  if (fixed + chunk_bytes(1) > kScratchBytes)
     return fail(MRA_EINVAL,
                 "this configuration needs at least %zu bytes of scratch for one image; the reserved array holds %zu",
-                fixed + per_img + 4096, kScratchBytes);
-  int64_t chunk = static_cast<int64_t>((kScratchBytes - fixed - 4096) / per_img);
+                fixed + chunk_bytes(1), kScratchBytes);
+  const size_t per_img = static_cast<size_t>(S) * NB * sizeof(float2) + sizeof(unsigned long long);
+  int64_t chunk = static_cast<int64_t>((kScratchBytes - fixed) / per_img);
   // images of a chunk index the polar kernel's grid.y and its row tiles the
   // contraction kernel's grid.y (both <= 65535)
   if (chunk > 65535) chunk = 65535;
   if (chunk > int64_t(65535) * mra::kTile / S) chunk = int64_t(65535) * mra::kTile / S;
-  while (chunk > 1) {  // leave room for tile padding and alignment
-    const int64_t tiles = (chunk * S + mra::kTile - 1) / mra::kTile;
-    const size_t need = align256(sizeof(unsigned long long) * chunk) +
-                        static_cast<size_t>(tiles) * NB * mra::kTile * sizeof(float2);
-    if (fixed + need <= kScratchBytes) break;
-    --chunk;
-  }
+  if (chunk < 1) chunk = 1;
+  while (chunk > 1 && fixed + chunk_bytes(chunk) > kScratchBytes) --chunk;  // tile padding and alignment
   unsigned long long *d_best = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * chunk));
   float2 *d_A = reinterpret_cast<float2 *>(base + off);
   const int64_t a_tiles = (chunk * S + mra::kTile - 1) / mra::kTile;
   const size_t a_bytes = static_cast<size_t>(a_tiles) * NB * mra::kTile * sizeof(float2);
-  if (off + a_bytes > kScratchBytes) return fail(MRA_EINVAL, "scratch layout overflow (internal)");
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 #define MRA_COPY(dst, src, bytes)                                                               \
   do {                                                                                          \
     cudaError_t ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);              \
-    if (ce != cudaSuccess) return fail(MRA_ECUDA, "table copy: %s", cudaGetErrorString(ce));    \
+    if (ce != cudaSuccess) return fail_sync(st, MRA_ECUDA, "table copy: %s", cudaGetErrorString(ce));    \
   } while (0)
   MRA_COPY(d_offs, h_offs, sizeof(float2) * NS);
   MRA_COPY(d_rings, h_rings, sizeof(int4) * NR);
@@ -266,7 +286,7 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(d_B, 0, b_bytes, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(d_A, 0, a_bytes, st)) != cudaSuccess)
-    return fail(MRA_ECUDA, "cudaMemsetAsync(scratch): %s", cudaGetErrorString(e));
+    return fail_sync(st, MRA_ECUDA, "cudaMemsetAsync(scratch): %s", cudaGetErrorString(e));
 
   // reference spectra (weighted), then the chunks of particles
   mra::PolarArgs pr{};
@@ -277,7 +297,7 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
   pr.weighted = true;
   pr.out = d_B;
   if ((e = mra::launch_polar(g, pr, st)) != cudaSuccess)
-    return fail(MRA_ECUDA, "reference polar kernel: %s", cudaGetErrorString(e));
+    return fail_sync(st, MRA_ECUDA, "reference polar kernel: %s", cudaGetErrorString(e));
   const int64_t LL = int64_t(c.L) * c.L;
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cnt = (n - c0 < chunk) ? n - c0 : chunk;
@@ -289,9 +309,9 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
     pa.weighted = false;
     pa.out = d_A;
     if ((e = mra::launch_polar(g, pa, st)) != cudaSuccess)
-      return fail(MRA_ECUDA, "particle polar kernel: %s", cudaGetErrorString(e));
+      return fail_sync(st, MRA_ECUDA, "particle polar kernel: %s", cudaGetErrorString(e));
     if ((e = cudaMemsetAsync(d_best, 0, sizeof(unsigned long long) * cnt, st)) != cudaSuccess)
-      return fail(MRA_ECUDA, "cudaMemsetAsync(keys): %s", cudaGetErrorString(e));
+      return fail_sync(st, MRA_ECUDA, "cudaMemsetAsync(keys): %s", cudaGetErrorString(e));
     mra::CCArgs ca{};
     ca.A = d_A;
     ca.B = d_B;
@@ -303,17 +323,17 @@ int mra_align_static(const mra_config_t *cfg, const float *d_refs, int32_t K, co
     ca.wait_limit = 2000;  // ~1 s of 0.5 ms polls
     ca.first_wait_limit = 2000;
     if ((e = mra::launch_cc_fp32(g, ca, st)) != cudaSuccess)
-      return fail(MRA_ECUDA, "contraction kernel: %s", cudaGetErrorString(e));
+      return fail_sync(st, MRA_ECUDA, "contraction kernel: %s", cudaGetErrorString(e));
     if ((e = mra::launch_decode(g, d_best, cnt, K, d_poses + c0, st)) != cudaSuccess)
-      return fail(MRA_ECUDA, "decode kernel: %s", cudaGetErrorString(e));
+      return fail_sync(st, MRA_ECUDA, "decode kernel: %s", cudaGetErrorString(e));
   }
   // Host-synchronous: the next call reuses the array, and a kernel that gave
   // up a bounded wait is reported here.
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
-    return fail(MRA_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    return fail_sync(st, MRA_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
   int flag = 0;
   if ((e = cudaMemcpy(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return fail(MRA_ECUDA, "read failure flag: %s", cudaGetErrorString(e));
+    return fail_sync(st, MRA_ECUDA, "read failure flag: %s", cudaGetErrorString(e));
   if (flag) return fail(MRA_ETIMEOUT, "a kernel gave up waiting for its bulk copies; the poses are invalid");
   return MRA_OK;
 }

@@ -1,6 +1,7 @@
-// Polar resampling and ring FFT (Algorithm 1: "convert x_i to polar
-// coordinates with given shift and apply FFT"; for the references the same
-// with no shift, followed by the ring weights of the Sec. 2 quadrature).
+// Polar resampling and ring FFT (Alg. 1, shift-loop conversion step: each
+// particle is resampled on the rings about its shifted centre and every ring
+// is Fourier transformed; the references get the same with no shift,
+// followed by the ring weights of the Sec. 2 quadrature).
 //
 // A CTA stages one image in shared memory and walks groups of R consecutive
 // rows (row = image * rows_per_img + shift): the groups blockIdx.x,

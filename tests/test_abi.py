@@ -107,3 +107,44 @@ def test_used_configs_pass_the_shared_memory_check(lib, cfg, precision):
         assert e.code == mra.MRA_ECUDA, str(e)
     else:
         lib.mra_destroy(h)
+
+
+def _static_call(lib, **kw):
+    """mra_align_static with NULL buffers: only the checks before any CUDA call can run."""
+    base = dict(L=32, first_ring=1, last_ring=5, ring_step=1, shift_range=1.0, shift_step=1.0, mirror=1,
+                precision=mra.MRA_FP32, chunk_images=0)
+    base.update(kw)
+    cfg = mra.MRAConfig(*(base[f] for f, _ in mra.MRAConfig._fields_))
+    buf = ctypes.create_string_buffer(512)
+    rc = lib.mra_align_static(ctypes.byref(cfg), None, 3, None, 0, None, None, buf, len(buf))
+    return rc, buf.value.decode()
+
+
+@pytest.mark.parametrize("kw,code,needle", [
+    # 50001 x 50001 shifts: the grid size must be checked without integer overflow
+    (dict(shift_range=25000.0, shift_step=1.0), mra.MRA_EINVAL, "4096"),
+    (dict(shift_range=float("inf"), shift_step=1.0), mra.MRA_EINVAL, "shift_range"),
+    (dict(shift_range=1.0, shift_step=float("inf")), mra.MRA_EINVAL, "shift_step"),
+    (dict(shift_range=float("nan")), mra.MRA_EINVAL, "shift_range"),
+    (dict(last_ring=90), mra.MRA_EINVAL, "M = 1024"),
+    (dict(L=31), mra.MRA_EINVAL, "L must be even"),
+    # the same shared-memory admission as mra_create (the FP32 contraction CTA of M = 512 fits; a
+    # 1024-pixel box does not fit the polar kernel's staged image)
+    (dict(L=1024, first_ring=1, last_ring=60), mra.MRA_EUNSUPPORTED, "shared memory"),
+    (dict(precision=mra.MRA_BF16_RESCORE), mra.MRA_EUNSUPPORTED, "FP32 path only"),
+])
+def test_static_entry_checks_the_configuration_like_create(lib, kw, code, needle):
+    rc, msg = _static_call(lib, **kw)
+    assert rc == code, msg
+    assert needle in msg, msg
+
+
+def test_static_entry_and_create_agree_on_every_rejection(lib):
+    for kw in (dict(shift_range=25000.0), dict(shift_range=float("inf")), dict(L=1024, last_ring=60),
+               dict(ring_step=0), dict(mirror=3)):
+        rc, msg = _static_call(lib, **kw)
+        cfg = dict(L=32, first_ring=1, last_ring=5, shift_range=1.0, shift_step=1.0)
+        cfg.update(kw)
+        with pytest.raises(mra.MRAError) as ei:
+            mra.mra_create(**cfg)
+        assert ei.value.code == rc and str(ei.value).endswith(msg), (kw, rc, msg, str(ei.value))
