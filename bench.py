@@ -189,16 +189,23 @@ def run_reference(args):
     import numpy as np
     import synth
     w = synth.WORKLOADS[args.workload]
-    sample = 16
-    refs, imgs, _, _ = synth.make_workload(w, n=max(sample, 64))
+    # each step a bounded sample (one image per host core, 16 on the GPU machine), and every step a
+    # different slice of a 400-image subset of the stack, so the timed steps together cover
+    # hundreds of distinct images
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    sample = max(8, min(16, cores))
+    pool_n = 400
+    refs, imgs, _, _ = synth.make_workload(w, n=pool_n)
     refs_np = refs.double().numpy()
     imgs_np = imgs.double().numpy()
     times = []
     for step in range(args.warmup + args.steps):
-        r = cpu_baseline(w, sample, refs_np, imgs_np[:sample])
+        lo = (step * sample) % (pool_n - sample + 1)
+        r = cpu_baseline(w, sample, refs_np, imgs_np[lo:lo + sample])
         if step >= args.warmup:
             times.append(r)
     value = statistics.mean(t["value"] for t in times)
+    covered = min(pool_n, (args.warmup + args.steps) * sample)
     ms = 1000.0 * w.n / value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -207,9 +214,10 @@ def run_reference(args):
                        "S": int(round(2 * w.shift_range / w.shift_step + 1)) ** 2,
                        "rings": f"{w.first_ring}..{w.last_ring}",
                        "mirror": 1, "path": "FP64 oracle (explicit DFT sums)",
-                       "step": f"{sample} images per step, scaled to the stack"},
+                       "step": f"{sample} images per step (a different slice of a {pool_n}-image subset each "
+                               f"step, {covered} distinct images over the run), scaled to the stack"},
             "cpu_baseline": {"value": value, "unit": "images/s", "cores": times[-1]["cores"], "kind": "oracle",
-                             "sample": times[-1]["sample"]},
+                             "sample": f"{covered} distinct images of the stack, {sample} per step; " + times[-1]["sample"]},
             "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -247,9 +255,18 @@ def main():
     cpu_line = None
     refs_np = imgs_np = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r64, i64, _, _ = synth.make_workload(w, n=48)
+        # the 200-image oracle subset of the stack (about 25 s on 16 host cores at 100 references and
+        # 81 shifts); with rings beyond 40 (M = 512: the 128-pixel, 200-reference workload) an image
+        # costs ~30x more and the sample is one image per core
+        n_cpu = 200 if w.last_ring <= 40 else 16
+        r64, i64, _, _ = synth.make_workload(w, n=n_cpu)
         refs_np, imgs_np = r64.double().numpy(), i64.double().numpy()
-        cpu_line = cpu_baseline(w, 48, refs_np, imgs_np)
+        cpu_line = cpu_baseline(w, n_cpu, refs_np, imgs_np)
+        # the 500-image, K = 10, 25-shift workload, every image (about 2 s)
+        w1 = synth.WORKLOADS["mra_n500_L76_K10_shift2"]
+        r1, i1, _, _ = synth.make_workload(w1)
+        full1 = cpu_baseline(w1, w1.n, r1.double().numpy(), i1.double().numpy())
+        cpu_line["mra_n500_L76_K10_shift2"] = {k: full1[k] for k in ("value", "unit", "cores", "sample", "seconds")}
 
     # inputs: rank r renders its own particles (weak scaling)
     wr = synth.Workload(**{**w.__dict__, "seed_particles": w.seed_particles + 100 * rank,
@@ -396,9 +413,6 @@ def main():
                              "M = 256, inverse-DFT flops at the BF16 peak; FP32: polar rows, FP32 contraction / "
                              "inverse DFT and the 8 rescored rows per image; HBM: stack read twice, spectra "
                              "written and read once, row maxima); frac = the largest / measured step time"}
-        tensor = None
-        if tensor:
-            roofline["tensor"] = tensor
         return {"label": label, "al": al, "value": n * world / (ms_step / 1000.0), "ms_step": ms_step,
                 "prof": prof, "roofline": roofline, "clocks": clk, "info": info, "step_roofline": step_roof,
                 "gpu_launches": sum(v["launches"] for v in prof.values())}

@@ -69,6 +69,16 @@ enum mra_precision {
     MRA_FP16_RESCORE = 2   /* FP16 tensor-core contraction, top-8 rows rescored in FP32    */
 };
 
+/* Tensor-core kernel of the 16-bit paths when M = 256 (rings up to 40); the
+ * two compute the same table and differ only in speed.  Other M and the
+ * FP32 path ignore the choice. */
+enum mra_kernel {
+    MRA_KERNEL_AUTO = 0,     /* the library's default (MRA_KERNEL_MMA_SYNC)                    */
+    MRA_KERNEL_MMA_SYNC = 1, /* warp-level mma.sync, tiles of 8 rows x 8 references            */
+    MRA_KERNEL_TCGEN05 = 2   /* tcgen05.mma with TMEM accumulators and TMA tensor-map staging,
+                                tiles of 16 rows x 8 references (k_umma256.cu)                  */
+};
+
 /* Search configuration.  Validated by mra_create:
  *   L even, 8 <= L <= 1024; 1 <= first_ring <= last_ring; ring_step >= 1;
  *   16 <= M <= 512 (so 3 <= last ring radius <= 81);
@@ -76,13 +86,16 @@ enum mra_precision {
  *   (to 1e-6), S <= 4096; mirror 0 or 1; precision one of mra_precision.
  *   Rings may reach outside the box; samples there read as zero.
  *   chunk_images: images per internal chunk (0 = sized from a 2 GiB
- *   workspace budget). */
+ *   workspace budget).  kernel: one of mra_kernel (0 = default); the
+ *   autotuner of the Python package picks it (and chunk_images) per
+ *   configuration by measurement. */
 typedef struct {
     int32_t L, first_ring, last_ring, ring_step;
     float shift_range, shift_step;
     int32_t mirror;
     int32_t precision;
     int32_t chunk_images;
+    int32_t kernel;
 } mra_config_t;
 
 /* Per-image result (Alg. 1, parameter-lookup step: the alignment

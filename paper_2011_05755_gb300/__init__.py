@@ -20,7 +20,8 @@ import torch
 
 __all__ = [
     "MRA_OK", "MRA_EINVAL", "MRA_ESTATE", "MRA_ENOMEM", "MRA_ECUDA", "MRA_ETIMEOUT", "MRA_EUNSUPPORTED",
-    "MRA_FP32", "MRA_BF16_RESCORE", "MRA_FP16_RESCORE", "MRAError", "MRAConfig", "MRAInfo", "POSE_FIELDS",
+    "MRA_FP32", "MRA_BF16_RESCORE", "MRA_FP16_RESCORE", "MRA_KERNEL_AUTO", "MRA_KERNEL_MMA_SYNC",
+    "MRA_KERNEL_TCGEN05", "MRAError", "MRAConfig", "MRAInfo", "POSE_FIELDS",
     "library_path", "load_library", "mra_create", "mra_destroy", "mra_last_error", "mra_get_info",
     "mra_set_refs", "mra_align", "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host",
     "mra_debug_polar", "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync",
@@ -30,6 +31,7 @@ __all__ = [
 
 MRA_OK, MRA_EINVAL, MRA_ESTATE, MRA_ENOMEM, MRA_ECUDA, MRA_ETIMEOUT, MRA_EUNSUPPORTED = range(7)
 MRA_FP32, MRA_BF16_RESCORE, MRA_FP16_RESCORE = 0, 1, 2
+MRA_KERNEL_AUTO, MRA_KERNEL_MMA_SYNC, MRA_KERNEL_TCGEN05 = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -55,7 +57,8 @@ class MRAError(RuntimeError):
 class MRAConfig(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("first_ring", ctypes.c_int32), ("last_ring", ctypes.c_int32),
                 ("ring_step", ctypes.c_int32), ("shift_range", ctypes.c_float), ("shift_step", ctypes.c_float),
-                ("mirror", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk_images", ctypes.c_int32)]
+                ("mirror", ctypes.c_int32), ("precision", ctypes.c_int32), ("chunk_images", ctypes.c_int32),
+                ("kernel", ctypes.c_int32)]
 
 
 class MRAInfo(ctypes.Structure):
@@ -156,8 +159,10 @@ def _host_ptr(a, dtype, name: str):
 
 
 def mra_create(L: int, first_ring: int, last_ring: int, ring_step: int = 1, shift_range: float = 0.0,
-               shift_step: float = 1.0, mirror: int = 1, precision: int = MRA_FP32, chunk_images: int = 0):
-    cfg = MRAConfig(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, precision, chunk_images)
+               shift_step: float = 1.0, mirror: int = 1, precision: int = MRA_FP32, chunk_images: int = 0,
+               kernel: int = MRA_KERNEL_AUTO):
+    cfg = MRAConfig(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, precision, chunk_images,
+                    kernel)
     h = ctypes.c_void_p()
     lib = load_library()
     rc = lib.mra_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -274,7 +279,7 @@ def mra_align_static(refs: torch.Tensor, imgs: torch.Tensor, poses: torch.Tensor
     _check_stack(refs, L, "refs")
     _check_stack(imgs, L, "imgs")
     _check_poses(poses, imgs.shape[0])
-    cfg = MRAConfig(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, MRA_FP32, 0)
+    cfg = MRAConfig(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, MRA_FP32, 0, 0)
     buf = ctypes.create_string_buffer(512)
     rc = load_library().mra_align_static(ctypes.byref(cfg), _dev_ptr(refs, torch.float32, "refs"), refs.shape[0],
                                          _dev_ptr(imgs, torch.float32, "imgs"), imgs.shape[0],
@@ -309,10 +314,10 @@ class Aligner:
     """Owns one library handle: references resident on the device, workspace reused."""
 
     def __init__(self, L, first_ring, last_ring, ring_step=1, shift_range=0.0, shift_step=1.0, mirror=1,
-                 precision=MRA_FP32, chunk_images=0):
+                 precision=MRA_FP32, chunk_images=0, kernel=MRA_KERNEL_AUTO):
         self.L = L
         self.h = mra_create(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, precision,
-                            chunk_images)
+                            chunk_images, kernel)
         self.K = 0
 
     def close(self):

@@ -19,6 +19,8 @@
 
 namespace mra {
 
+// Neumaier's compensated addition: s + v into (s, c), with c gathering the
+// rounding error of every addition (the total is s + c).
 __device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
   const float t = s + v;
   if (fabsf(s) >= fabsf(v))
@@ -234,11 +236,33 @@ __global__ void avg_finalize_kernel(int LL, const float *sum, const float *comp,
   }
 }
 
+// Compensated sum over the CTA of each thread's (s, c), in a fixed tree
+// order (deterministic); returns s + c to every thread.
+__device__ __forceinline__ float cta_sum_compensated(float s, float c, float *rs, float *rc) {
+  rs[threadIdx.x] = s;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      float a = rs[threadIdx.x], ca = rc[threadIdx.x] + rc[threadIdx.x + w];
+      neumaier_add(a, ca, rs[threadIdx.x + w]);
+      rs[threadIdx.x] = a;
+      rc[threadIdx.x] = ca;
+    }
+    __syncthreads();
+  }
+  const float total = rs[0] + rc[0];
+  __syncthreads();
+  return total;
+}
+
 // Requires n >= 1 (the C-ABI layer handles n == 0).
 // Reference refresh: reseed empty classes from a chosen image, then
 // normalise every populated (or reseeded) class to zero mean and unit
-// standard deviation over the box.  One CTA per class; two-pass (mean,
-// then centred second moment) in FP32 with a fixed reduction order.
+// standard deviation over the box.  One CTA per class; two passes (the
+// mean, then the centred second moment), each summed in FP32 with Neumaier
+// compensation in a fixed reduction order; 1 / sqrt(var) from correctly
+// rounded square root and division.
 __global__ void __launch_bounds__(256) refresh_refs_kernel(int L, float *refs, const int *counts, const int *reseed,
                                                            const float *imgs, int64_t n) {
   const int k = blockIdx.x;
@@ -252,30 +276,18 @@ __global__ void __launch_bounds__(256) refresh_refs_kernel(int L, float *refs, c
     for (int i = threadIdx.x; i < LL; i += blockDim.x) r[i] = im[i];
     __syncthreads();
   }
-  __shared__ float red[256];
-  float s = 0.f;
-  for (int i = threadIdx.x; i < LL; i += blockDim.x) s += r[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  const float mean = red[0] / static_cast<float>(LL);
-  __syncthreads();
-  float q = 0.f;
+  __shared__ float rs[256], rc[256];
+  float s = 0.f, c = 0.f;
+  for (int i = threadIdx.x; i < LL; i += blockDim.x) neumaier_add(s, c, r[i]);
+  const float mean = cta_sum_compensated(s, c, rs, rc) / static_cast<float>(LL);
+  s = 0.f;
+  c = 0.f;
   for (int i = threadIdx.x; i < LL; i += blockDim.x) {
     const float d = r[i] - mean;
-    q = fmaf(d, d, q);
+    neumaier_add(s, c, d * d);
   }
-  red[threadIdx.x] = q;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  const float var = red[0] / static_cast<float>(LL);
-  const float inv = var > 0.f ? rsqrtf(var) : 0.f;
+  const float var = cta_sum_compensated(s, c, rs, rc) / static_cast<float>(LL);
+  const float inv = var > 0.f ? __fdiv_rn(1.0f, __fsqrt_rn(var)) : 0.f;
   for (int i = threadIdx.x; i < LL; i += blockDim.x) r[i] = (r[i] - mean) * inv;
 }
 

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 
 #include "mra_internal.h"
@@ -44,7 +45,12 @@ struct mra_handle {
   bool fp16 = false;           // FP16 rather than BF16 operands
   uint2 *B16 = nullptr;        // reference B fragments
   int B16_refs = 0;            // references (padded) the fragment buffer holds
-  uint4 *A16 = nullptr;        // particle A fragments for one chunk
+  uint4 *A16 = nullptr;        // particle A fragments for one chunk (mma.sync kernels), or
+                               // the k-step tiles of the tcgen05 kernel (umma)
+  bool umma = false;           // M = 256 precision split on tcgen05 (k_umma256.cu)
+  void *B16u = nullptr;        // reference k-step tiles of the tcgen05 kernel
+  int B16u_refs = 0;           // references (padded to tiles) the tiles hold
+  CUtensorMap tmA{}, tmB{};    // TMA descriptors of the particle / reference k-step tiles
   size_t A16_bytes = 0;
   float *rowmax = nullptr;     // [chunk][K][S][2]
   int64_t rowmax_cap = 0;      // floats
@@ -279,6 +285,8 @@ int check_config(const mra_config_t *c, char *why, size_t why_len) {
   if (c->precision != MRA_FP32 && c->precision != MRA_BF16_RESCORE && c->precision != MRA_FP16_RESCORE)
     return bad("precision must be MRA_FP32, MRA_BF16_RESCORE or MRA_FP16_RESCORE");
   if (c->chunk_images < 0) return bad("chunk_images must be >= 0");
+  if (c->kernel != MRA_KERNEL_AUTO && c->kernel != MRA_KERNEL_MMA_SYNC && c->kernel != MRA_KERNEL_TCGEN05)
+    return bad("kernel must be MRA_KERNEL_AUTO, MRA_KERNEL_MMA_SYNC or MRA_KERNEL_TCGEN05");
   // the largest ring sets M = its ring length
   const long long r_max = c->first_ring + (static_cast<long long>(c->last_ring - c->first_ring) / c->ring_step) *
                                               c->ring_step;
@@ -532,10 +540,97 @@ int build_tables(mra_handle *h) {
     }
     if ((rc = upload(h, frag, &g.dft16, "DFT fragments"))) return rc;
   }
+  // tcgen05 path (M = 256): frequencies four to an MMA.  Greedy in f order:
+  // a group takes the next frequencies while it has fewer than four; its
+  // k-step count is that of its first (lowest) frequency, the largest, as
+  // R_f does not grow with f; the others are padded with zero k-steps.
+  h->umma = h->half && M == 256 && c.kernel == MRA_KERNEL_TCGEN05;
+  if (M == 256) {
+    std::vector<int> gfreq, uinfo, umap(kso[H + 1], -1);
+    int NG = 0, NU = 0;
+    for (int f = 0; f <= H;) {
+      const int nks = kso[f + 1] - kso[f];
+      int members[4] = {-1, -1, -1, -1};
+      for (int sl = 0; sl < 4 && f <= H; ++sl, ++f) {
+        members[sl] = f;
+        for (int j = 0; j < kso[f + 1] - kso[f]; ++j) umap[kso[f] + j] = (NU + j) * 4 + sl;
+      }
+      for (int sl = 0; sl < 4; ++sl) gfreq.push_back(members[sl]);
+      for (int j = 0; j < nks; ++j) uinfo.push_back(NG | (j << 8) | ((j == nks - 1 ? 1 : 0) << 10));
+      NU += nks;
+      ++NG;
+    }
+    if (NU > mra::kUmmaMaxU || NG > mra::kUmmaMaxG)
+      return set_err(h, MRA_EINVAL, "%d MMA k-steps in %d groups exceed the tcgen05 tables", NU, NG);
+    h->g.NU = NU;
+    h->g.NG = NG;
+    if ((rc = upload(h, umap, &h->g.umap, "k-step map"))) return rc;
+    if ((rc = upload(h, uinfo, &h->g.uinfo, "k-step groups"))) return rc;
+    if ((rc = upload(h, gfreq, &h->g.gfreq, "group frequencies"))) return rc;
+    // BF16 16-point DFT matrices in the canonical K-major layout (B operands,
+    // 32 N-rows x 32 K): W1[(c', k)][(a, c)] and W2[(c'', j)][(t, c')] with
+    // K = 2 a + c: [[cos, -sin], [sin, cos]] of 2 pi a k / 16 (resp. t j).
+    auto bf16 = [](double v) {  // round to nearest even (|v| <= 1)
+      const float x = static_cast<float>(v);
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      return static_cast<uint16_t>((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+    };
+    std::vector<uint16_t> w16(2048, 0);
+    for (int m = 0; m < 2; ++m)
+      for (int n = 0; n < 32; ++n)
+        for (int K = 0; K < 32; ++K) {
+          const int co = n >> 4, x = n & 15, ci = K & 1, y = K >> 1;
+          const double th = kTwoPi * x * y / 16.0;
+          const double v = co == ci ? std::cos(th) : (co == 0 ? -std::sin(th) : std::sin(th));
+          w16[m * 1024 + ((n >> 3) * 512 + (K >> 3) * 128 + (n & 7) * 16 + (K & 7) * 2) / 2] = bf16(v);
+        }
+    std::vector<uint32_t> wpk(1024);
+    for (int i = 0; i < 1024; ++i) wpk[i] = w16[2 * i] | (static_cast<uint32_t>(w16[2 * i + 1]) << 16);
+    if ((rc = upload(h, wpk, &h->g.idft_w, "inverse-DFT matrices"))) return rc;
+    std::vector<float2> tw(256);
+    for (int t = 0; t < 16; ++t)
+      for (int k = 0; k < 16; ++k) {
+        const double th = kTwoPi * t * k / 256.0;
+        tw[t * 16 + k] = make_float2(static_cast<float>(std::cos(th)), static_cast<float>(std::sin(th)));
+      }
+    if ((rc = upload(h, tw, &h->g.idft_tw, "inverse-DFT twiddles"))) return rc;
+  }
   if ((rc = dev_alloc(h, &h->d_err, sizeof(int), "failure flags"))) return rc;
   h->tables.push_back(h->d_err);
   cudaError_t e = cudaMemset(h->d_err, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_err(h, e, "cudaMemset(failure flags)");
+  return MRA_OK;
+}
+
+// TMA descriptor of a buffer of k-step tiles seen as a 2-D tensor of 16-bit
+// elements with rows of 256 bytes (128 elements); one load box is one tile
+// of box_rows rows (4 KB particle tiles: 16 rows; 2 KB reference tiles: 8).
+// cuTensorMapEncodeTiled comes from the driver through the runtime's entry
+// point query, so the library needs no link to libcuda.
+int make_tile_map(mra_handle *h, CUtensorMap *tm, void *base, uint64_t rows, uint32_t box_rows, const char *what) {
+  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return set_err(h, MRA_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    }
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  const cuuint64_t dims[2] = {128, rows};
+  const cuuint64_t strides[1] = {256};
+  const cuuint32_t box[2] = {128, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, base, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_err(h, MRA_ECUDA, "cuTensorMapEncodeTiled(%s) failed with %d", what, int(r));
   return MRA_OK;
 }
 
@@ -546,6 +641,7 @@ int ensure_chunk_workspace(mra_handle *h) {
   if (!h->best) {
     size_t per_img = h->half ? static_cast<size_t>(S) * h->g.KS * 64 + static_cast<size_t>(h->K) * S * 8
                              : static_cast<size_t>(S) * h->NB * sizeof(float2);
+    if (h->umma) per_img = static_cast<size_t>(S) * h->g.NU * 256 + static_cast<size_t>(h->K) * S * 8;
     int chunk = h->cfg.chunk_images;
     if (chunk <= 0) {
       const size_t budget = size_t(2) << 30;
@@ -560,7 +656,19 @@ int ensure_chunk_workspace(mra_handle *h) {
     h->chunk = chunk;
     const int64_t tiles = (int64_t(chunk) * S + mra::kTile - 1) / mra::kTile;
     int rc;
-    if (h->half) {
+    if (h->umma) {
+      // k-step tiles of 16 rows; slots and k-steps no frequency fills are
+      // never written and must read as zero
+      const int64_t utiles = (int64_t(chunk) * S + mra::kUmmaRows - 1) / mra::kUmmaRows;
+      h->A16_bytes = static_cast<size_t>(utiles) * h->g.NU * 4096;
+      if ((rc = dev_alloc(h, &h->A16, h->A16_bytes, "particle k-step tiles"))) return rc;
+      cudaError_t e = cudaMemset(h->A16, 0, h->A16_bytes);
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaMemset(particle k-step tiles)");
+      if ((rc = make_tile_map(h, &h->tmA, h->A16, static_cast<uint64_t>(utiles) * h->g.NU * 16, 16,
+                              "particle k-step tiles")))
+        return rc;
+      if ((rc = dev_alloc(h, &h->cand, sizeof(int) * mra::kTopRows * chunk, "candidate rows"))) return rc;
+    } else if (h->half) {
       h->A16_bytes = static_cast<size_t>(tiles) * h->g.KS * 512;
       if ((rc = dev_alloc(h, &h->A16, h->A16_bytes, "particle fragments"))) return rc;
       if ((rc = dev_alloc(h, &h->cand, sizeof(int) * mra::kTopRows * chunk, "candidate rows"))) return rc;
@@ -647,6 +755,7 @@ void free_all(mra_handle *h) {
   fr(h->best);
   fr(h->B16);
   fr(h->A16);
+  fr(h->B16u);
   fr(h->rowmax);
   fr(h->cand);
   mra::AvgWork &w = h->avg;
@@ -706,6 +815,7 @@ int run_polar(mra_handle *h, const float *imgs, int64_t n, int rows_per_img, boo
   a.dbg_spec = dbg_spec;
   a.out16 = out16;
   a.fp16 = h->fp16;
+  a.umma = h->umma && out16 != nullptr;
   const int rc = check_launch(h, mra::launch_polar(h->g, a, st), "polar/ring-FFT kernel");
   prof_end(h, rec, 1, st);
   return rc;
@@ -729,7 +839,13 @@ int align_chunk_half(mra_handle *h, const float *imgs, int64_t cnt, mra_pose_t *
   t.wait_limit = kWaitLimit;
   t.first_wait_limit = first_wait_limit();
   int rec = prof_begin(h, MRA_STAGE_CC, st);
-  rc = check_launch(h, mra::launch_cc_tc(h->g, t, h->fp16, st), "tensor-core contraction/IFFT kernel");
+  if (h->umma) {
+    t.B16 = static_cast<const uint2 *>(h->B16u);
+    rc = check_launch(h, mra::launch_cc_umma256(&h->tmA, &h->tmB, h->g, t, h->fp16, st),
+                      "tcgen05 contraction/IFFT kernel");
+  } else {
+    rc = check_launch(h, mra::launch_cc_tc(h->g, t, h->fp16, st), "tensor-core contraction/IFFT kernel");
+  }
   prof_end(h, rec, 1, st);
   if (rc) return rc;
   rec = prof_begin(h, MRA_STAGE_RESCORE, st);
@@ -866,7 +982,25 @@ int mra_set_refs(mra_t h, const float *d_refs, int32_t K, mra_stream_t stream) {
   cudaError_t e = cudaMemsetAsync(h->B, 0, static_cast<size_t>(Kpad) * h->NB * sizeof(float2), st);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaMemsetAsync(reference spectra)");
   if (int rc = run_polar(h, d_refs, K, 1, false, true, h->B, nullptr, nullptr, st)) return rc;
-  if (h->half) {
+  if (h->umma) {
+    const int ktiles = Kpad / mra::kUmmaRefs;
+    if (!h->B16u || Kpad > h->B16u_refs) {
+      dev_free(h, h->B16u, static_cast<size_t>(h->B16u_refs / mra::kUmmaRefs) * h->g.NU * 2048);
+      h->B16u = nullptr;
+      h->B16u_refs = 0;
+      if (int rc = dev_alloc(h, &h->B16u, static_cast<size_t>(ktiles) * h->g.NU * 2048, "reference k-step tiles"))
+        return rc;
+      h->B16u_refs = Kpad;
+      if (int rc = make_tile_map(h, &h->tmB, h->B16u, static_cast<uint64_t>(ktiles) * h->g.NU * 8, 8,
+                                 "reference k-step tiles"))
+        return rc;
+    }
+    const int rec = prof_begin(h, MRA_STAGE_CONVERT, st);
+    const int rc = check_launch(h, mra::launch_refs16u(h->g, h->B, ktiles, h->B16u, h->fp16, st),
+                                "reference k-step tile kernel");
+    prof_end(h, rec, 1, st);
+    if (rc) return rc;
+  } else if (h->half) {
     const size_t b16 = static_cast<size_t>(Kpad / mra::kTile) * 2 * h->g.KS * 32 * sizeof(uint2);
     if (!h->B16 || Kpad > h->B16_refs) {
       dev_free(h, h->B16, static_cast<size_t>(h->B16_refs / mra::kTile) * 2 * h->g.KS * 32 * sizeof(uint2));
@@ -893,8 +1027,9 @@ int mra_copy_refs(mra_t dst, mra_t src, mra_stream_t stream) {
   const mra_config_t &a = dst->cfg, &b = src->cfg;
   if (a.L != b.L || a.first_ring != b.first_ring || a.last_ring != b.last_ring || a.ring_step != b.ring_step ||
       a.shift_range != b.shift_range || a.shift_step != b.shift_step || a.mirror != b.mirror ||
-      a.precision != b.precision)
-    return set_err(dst, MRA_EINVAL, "source and destination configurations differ (chunk_images may differ)");
+      a.precision != b.precision || dst->umma != src->umma)
+    return set_err(dst, MRA_EINVAL,
+                   "source and destination configurations differ (chunk_images may differ, the kernel may not)");
   if (src->device != dst->device) return set_err(dst, MRA_EINVAL, "source handle lives on another device");
   if (int rc = select_device(dst)) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -912,7 +1047,23 @@ int mra_copy_refs(mra_t dst, mra_t src, mra_stream_t stream) {
   cudaError_t e = cudaMemcpyAsync(dst->B, src->B, static_cast<size_t>(Kpad) * dst->NB * sizeof(float2),
                                   cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_err(dst, e, "cudaMemcpyAsync(reference spectra)");
-  if (dst->half) {
+  if (dst->umma) {
+    const int ktiles = Kpad / mra::kUmmaRefs;
+    if (!dst->B16u || Kpad > dst->B16u_refs) {
+      dev_free(dst, dst->B16u, static_cast<size_t>(dst->B16u_refs / mra::kUmmaRefs) * dst->g.NU * 2048);
+      dst->B16u = nullptr;
+      dst->B16u_refs = 0;
+      if (int rc = dev_alloc(dst, &dst->B16u, static_cast<size_t>(ktiles) * dst->g.NU * 2048, "reference k-step tiles"))
+        return rc;
+      dst->B16u_refs = Kpad;
+      if (int rc = make_tile_map(dst, &dst->tmB, dst->B16u, static_cast<uint64_t>(ktiles) * dst->g.NU * 8, 8,
+                                 "reference k-step tiles"))
+        return rc;
+    }
+    e = cudaMemcpyAsync(dst->B16u, src->B16u, static_cast<size_t>(ktiles) * dst->g.NU * 2048,
+                        cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_err(dst, e, "cudaMemcpyAsync(reference k-step tiles)");
+  } else if (dst->half) {
     const size_t b16 = static_cast<size_t>(Kpad / mra::kTile) * 2 * dst->g.KS * 32 * sizeof(uint2);
     if (!dst->B16 || Kpad > dst->B16_refs) {
       dev_free(dst, dst->B16, static_cast<size_t>(dst->B16_refs / mra::kTile) * 2 * dst->g.KS * 32 * sizeof(uint2));

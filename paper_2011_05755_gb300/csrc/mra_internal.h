@@ -56,7 +56,23 @@ struct Geometry {
   // kTc256ChunkKs (M = 256) or kTc512ChunkKs (M = 512) k-steps.
   int NCH;
   const int *chunk_f;     // [NCH + 1]
+  // tcgen05 path (M = 256): frequencies packed four to an MMA.  A group holds
+  // up to four frequencies with the same number of 16-ring k-steps (fewer
+  // are padded with zero k-steps); MMA k-step u runs over (group, k-step).
+  int NU;                 // MMA k-steps per tile
+  int NG;                 // groups
+  const int *umap;        // [KS] k-step kso[f] + j of frequency f -> u * 4 + slot
+  const int *uinfo;       // [NU] group | (k-step in group) << 8 | (last k-step of the group) << 10
+  const int *gfreq;       // [NG * 4] frequency in each slot of a group, -1 if empty
+  const uint32_t *idft_w; // [1024] BF16 16-point DFT matrices W1, W2 (32 x 32, canonical K-major layout)
+  const float2 *idft_tw;  // [256] w256^(t k) = exp(2 pi i t k / 256) at [t * 16 + k]
 };
+
+// Tile of the tcgen05 M = 256 kernel and its table bounds.
+constexpr int kUmmaRows = 16;   // particle rows per tile
+constexpr int kUmmaRefs = 8;    // references per tile
+constexpr int kUmmaMaxU = 128;  // MMA k-steps per tile
+constexpr int kUmmaMaxG = 64;   // frequency groups
 
 constexpr int kTc256ChunkKs = 22;
 constexpr int kTc512ChunkKs = 44;
@@ -69,8 +85,10 @@ struct PolarArgs {
   bool use_shifts;     // false for references (s = 0)
   bool weighted;       // multiply bins by bweight (references)
   float2 *out;         // tiled spectra [ceil(rows/8)][NB][8] (may be null in debug)
-  uint4 *out16;        // 16-bit A fragments [ceil(rows/8)][KS][32 lanes] or null
+  uint4 *out16;        // 16-bit A fragments [ceil(rows/8)][KS][32 lanes], or (umma) k-step tiles
+                       // [ceil(rows/16)][NU][4096 B], or null
   bool fp16;           // out16 element type: FP16 (true) or BF16 (false)
+  bool umma;           // out16 in the tcgen05 k-step tile layout
   float *dbg_samples;  // [rows][NS] or null
   float2 *dbg_spec;    // [rows][NBIN] or null
 };
@@ -112,6 +130,13 @@ struct RescoreArgs {
 };
 
 cudaError_t launch_refs16(const Geometry &g, const float2 *B, int ktiles, uint2 *B16, bool fp16, cudaStream_t st);
+// tcgen05 path (M = 256): reference k-step tiles [ktiles][NU][2048 B], and the
+// contraction / inverse-DFT / row-maxima kernel.  tmA and tmB point to the
+// CUtensorMap of the particle and reference k-step tiles (2-D, 16-bit
+// elements, rows of 256 bytes; boxes of 16 and 8 rows).
+cudaError_t launch_refs16u(const Geometry &g, const float2 *B, int ktiles, void *B16u, bool fp16, cudaStream_t st);
+cudaError_t launch_cc_umma256(const void *tmA, const void *tmB, const Geometry &g, const TcArgs &a, bool fp16,
+                              cudaStream_t st);
 cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStream_t st);
 cudaError_t launch_top8(const float *rowmax, int64_t n, int nrows, int *cand, cudaStream_t st);
 cudaError_t launch_rescore(const Geometry &g, const RescoreArgs &a, cudaStream_t st);

@@ -33,13 +33,19 @@ namespace mra {
 __host__ __device__ inline int sample_stride(int NS) { return NS + ((16 - NS) & 31); }
 
 // Output layouts of the polar kernel: FP32 frequency-major tiles, or the
-// 16-bit q / p planes (BF16 or FP16) that phase 3 turns into mma fragments.
-enum PolarOut { kOutF32 = 0, kOutBF16 = 1, kOutF16 = 2 };
+// 16-bit q / p planes (BF16 or FP16) that phase 3 turns into mma.sync
+// fragments (kOutBF16, kOutF16) or into the k-step tiles of the tcgen05
+// path (kOutUBF16, kOutUF16: per tile of 16 rows and MMA k-step u a
+// 128 x 16 operand in the canonical K-major layout, row = frequency slot * 32
+// + (q|p) * 16 + row in tile; see k_umma256.cu).
+enum PolarOut { kOutF32 = 0, kOutBF16 = 1, kOutF16 = 2, kOutUBF16 = 3, kOutUF16 = 4 };
+__host__ __device__ constexpr bool out_is_fp16(int out) { return out == kOutF16 || out == kOutUF16; }
+__host__ __device__ constexpr bool out_is_umma(int out) { return out == kOutUBF16 || out == kOutUF16; }
 
 // (q, p) of one bin packed as a 16-bit pair word: q low, p high.
 template <int OUT>
 __device__ __forceinline__ uint32_t pack_qp(float q, float p) {
-  if constexpr (OUT == kOutF16) {
+  if constexpr (out_is_fp16(OUT)) {
     return static_cast<uint32_t>(__half_as_ushort(__float2half_rn(q))) |
            (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(p))) << 16);
   } else {
@@ -258,8 +264,35 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs
       i1 = i0;
     }
 
-    // Phase 3 (16-bit paths): fragment-order copy-out, 16 bytes per lane slot.
-    if constexpr (OUT != kOutF32) {
+    // Phase 3 (16-bit paths): copy-out in the layout of the tensor-core
+    // kernel, 16 bytes per store.
+    if constexpr (out_is_umma(OUT)) {
+      __syncthreads();
+      // job (row i, old k-step kk, half hh): 8 rings of one k-step; its q and
+      // p halves go to rows slot * 32 + row % 16 and slot * 32 + 16 + row % 16
+      // of MMA k-step tile u = umap[kk] / 4 (slot = umap[kk] % 4)
+      unsigned char *out = reinterpret_cast<unsigned char *>(a.out16);
+      for (int idx = threadIdx.x; idx < g.KS * 2 * nrows; idx += blockDim.x) {
+        const int i = idx % nrows, rem = idx / nrows;
+        const int hh = rem & 1, kk = rem >> 1;
+        const int64_t row = row0 + i;
+        const int um = __ldg(g.umap + kk);
+        const int u = um >> 2, slot = um & 3;
+        const uint32_t *w = planes + i * NB16 + kk * 16;
+        const int swz = kk & 14;
+        uint32_t wq[4], wp[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const uint2 v = *reinterpret_cast<const uint2 *>(w + ((8 * hh + 2 * jj) ^ swz));
+          wq[jj] = __byte_perm(v.x, v.y, 0x5410);  // q of rings 2jj, 2jj + 1
+          wp[jj] = __byte_perm(v.x, v.y, 0x7632);  // p of the same rings
+        }
+        unsigned char *blk = out + ((row >> 4) * g.NU + u) * 4096 + hh * 128;
+        const int mq = slot * 32 + static_cast<int>(row & 15), mp = mq + 16;
+        *reinterpret_cast<uint4 *>(blk + (mq >> 3) * 256 + (mq & 7) * 16) = make_uint4(wq[0], wq[1], wq[2], wq[3]);
+        *reinterpret_cast<uint4 *>(blk + (mp >> 3) * 256 + (mp & 7) * 16) = make_uint4(wp[0], wp[1], wp[2], wp[3]);
+      }
+    } else if constexpr (OUT != kOutF32) {
       __syncthreads();
       const int per_k = nrows * 4;
       for (int idx = threadIdx.x; idx < g.KS * per_k; idx += blockDim.x) {

@@ -1,0 +1,156 @@
+// Blackwell (sm_103a) tensor-core primitives written as inline PTX: tensor
+// memory (TMEM) allocation, loads and stores, the 5th-generation MMA
+// (tcgen05.mma, BF16/FP16 operands, FP32 accumulation in TMEM), its commit
+// to an mbarrier, shared-memory matrix descriptors, and TMA tensor-map loads.
+//
+// Operand layout used throughout (the "K-major, no swizzle" canonical
+// layout): a matrix of R rows by 16 K-elements (16-bit) is stored as core
+// matrices of 8 rows x 16 bytes (8 elements); element (row, k) sits at byte
+//     (row / 8) * SBO + (k / 8) * LBO + (row % 8) * 16 + (k % 8) * 2,
+// LBO being the distance between the two core matrices of a row group along
+// K and SBO the distance between consecutive groups of 8 rows.
+#pragma once
+
+#include <cstdint>
+
+#include "tma.cuh"
+
+namespace mra {
+
+// Shared-memory matrix descriptor (tcgen05 format): start address, LBO and
+// SBO in units of 16 bytes, descriptor version 1 (bits 46-47), no swizzle.
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16 with FP32 accumulation: A and B both
+// BF16 (bf16 = true) or both FP16, both K-major, N / 8 at bits 17-22,
+// M / 16 at bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
+__device__ __forceinline__ void umma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on `bar` once every tcgen05.mma this thread issued before has completed.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// TMEM allocation by one whole warp; the base address is written to *dst (shared).
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+// Warp-collective TMEM loads (lane i of the warp reads TMEM lane
+// (warp % 4) * 32 + i; columns are 32-bit): 16 or 32 consecutive columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// TMA load of one box of a 2-D tensor map into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Hint to bring `bytes` (a multiple of 16) of global memory at `src` into L2.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier that also gives up as soon
+// as another warp of the CTA has raised *abort.  On giving up (limit polls,
+// each sleeping up to kWaitHintNs) it raises *abort and the device error
+// flag.  Returns false on giving up or abort.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, uint32_t limit, volatile int *abort,
+                                              int *err) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  atomicOr(err, 1);
+  return false;
+}
+
+// Non-blocking test of an mbarrier phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// The same bounded wait by spinning instead of suspending, for the single
+// threads that issue TMA copies and MMAs (a suspended thread resumes later
+// than a spinning one sees the phase complete).  limit counts sleeps of the
+// suspending form; the spin checks the clock and gives up after about
+// limit * kWaitHintNs nanoseconds at the maximum SM clock (2.07 GHz).
+__device__ __forceinline__ bool spin_or_abort(uint64_t *bar, uint32_t parity, uint32_t limit, volatile int *abort,
+                                              int *err) {
+  if (limit == 0) {  // a zero limit gives up at once, like the suspending form
+    *abort = 1;
+    atomicOr(err, 1);
+    return false;
+  }
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long budget = static_cast<long long>(limit) * (kWaitHintNs * 2070ll / 1000);
+  const long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((i & 63) == 63) {
+      if (*abort) return false;
+      if (clock64() - t0 > budget) break;
+    }
+  }
+  *abort = 1;
+  atomicOr(err, 1);
+  return false;
+}
+
+}  // namespace mra

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_struct_layouts_match_header():
-    assert ctypes.sizeof(mra.MRAConfig) == 36
+    assert ctypes.sizeof(mra.MRAConfig) == 40
     assert ctypes.sizeof(mra.MRAInfo) == 40
     assert len(mra.POSE_FIELDS) == 8  # mra_pose_t is 8 x 4 bytes
 
@@ -55,6 +55,7 @@ def test_struct_layouts_match_header():
     (dict(L=32, first_ring=1, last_ring=5, shift_range=40.0, shift_step=1.0), "4096"),
     (dict(L=32, first_ring=1, last_ring=5, mirror=2), "mirror"),
     (dict(L=32, first_ring=1, last_ring=5, precision=7), "precision"),
+    (dict(L=32, first_ring=1, last_ring=5, kernel=3), "kernel"),
 ])
 def test_create_rejects_bad_config_before_touching_cuda(lib, kw, needle):
     with pytest.raises(mra.MRAError) as ei:
@@ -112,7 +113,7 @@ def test_used_configs_pass_the_shared_memory_check(lib, cfg, precision):
 def _static_call(lib, **kw):
     """mra_align_static with NULL buffers: only the checks before any CUDA call can run."""
     base = dict(L=32, first_ring=1, last_ring=5, ring_step=1, shift_range=1.0, shift_step=1.0, mirror=1,
-                precision=mra.MRA_FP32, chunk_images=0)
+                precision=mra.MRA_FP32, chunk_images=0, kernel=0)
     base.update(kw)
     cfg = mra.MRAConfig(*(base[f] for f, _ in mra.MRAConfig._fields_))
     buf = ctypes.create_string_buffer(512)

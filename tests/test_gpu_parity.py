@@ -17,6 +17,7 @@ import torch
 
 import synth
 from oracle import mra_oracle as O
+from oracle_pool import oracle_poses, table_value
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +47,9 @@ CASES = {
     "M16": (16, 1, 2, 1, 1.0, 1.0, 1, 2, 3),
     "M32": (16, 1, 4, 1, 1.0, 1.0, 1, 2, 3),
     "M64": (20, 1, 6, 1, 2.0, 1.0, 1, 9, 3),
+    # M = 256 with sparse rings (3, 6, ..., 24: other R_f and frequency groups) and K not a tile multiple
+    "M256_r24_step": (56, 3, 24, 3, 1.0, 1.0, 1, 13, 3),
+    "M256_nomirror": (64, 2, 30, 1, 2.0, 1.0, 0, 9, 3),
 }
 # FP32 only: rings beyond 64 at L = 132 exceed the shared memory of the
 # 16-bit paths' rescore CTA (mra_create reports MRA_EUNSUPPORTED for them)
@@ -147,15 +151,20 @@ def tc_tol(prec, M):
     return 8 * u + (4 * 2.0 ** -8 if M >= 256 else 0.0)
 
 
+KERNEL_CODE = {"default": 0, "mma_sync": 1, "tcgen05": 2}
+TC_CASES = [(name, "default") for name in ["M128_ragged", "M128_step2_nomirror", "M512_L128", "M16", "M64"]] + \
+    [("M256_L76", "mma_sync"), ("M256_L76", "tcgen05"), ("M256_r24_step", "tcgen05"), ("M256_nomirror", "tcgen05")]
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-@pytest.mark.parametrize("name", ["M128_ragged", "M128_step2_nomirror", "M256_L76", "M512_L128", "M16", "M64"])
-def test_stage_parity_tensor_core(mra, name, prec):
+@pytest.mark.parametrize("name,kernel", TC_CASES)
+def test_stage_parity_tensor_core(mra, name, kernel, prec):
     """The CC table from the 16-bit tensor-core contraction (before rescoring) against the oracle."""
     L, r1, r2, dr, R, step, mirror, K, n = CASES[name]
     refs, imgs = _inputs(L, K, n, R, mirror, seed=zlib.crc32(name.encode()) % 1000)
     cfg = O.MRAConfig(L, r1, r2, dr, R, step, mirror)
     precision = mra.MRA_BF16_RESCORE if prec == "bf16" else mra.MRA_FP16_RESCORE
-    al = mra.Aligner(L, r1, r2, dr, R, step, mirror, precision)
+    al = mra.Aligner(L, r1, r2, dr, R, step, mirror, precision, kernel=KERNEL_CODE[kernel])
     al.set_refs(refs.to(DEV))
     table = al.debug_cc(imgs.to(DEV)).cpu().numpy()
     ot = _oracle_table(imgs, refs, cfg)
@@ -168,13 +177,17 @@ def test_stage_parity_tensor_core(mra, name, prec):
     al.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
-@pytest.mark.parametrize("name", list(CASES))
-def test_pose_and_average_parity(mra, name, prec):
+POSE_CASES = [(name, prec, "default") for name in CASES for prec in ("fp32", "bf16", "fp16")] + \
+    [(name, prec, "tcgen05") for name in ("M256_L76", "M256_r24_step", "M256_nomirror") for prec in ("bf16", "fp16")]
+
+
+@pytest.mark.parametrize("name,prec,kernel", POSE_CASES)
+def test_pose_and_average_parity(mra, name, prec, kernel):
     L, r1, r2, dr, R, step, mirror, K, n = CASES[name]
     refs, imgs = _inputs(L, K, n + 6, R, mirror, seed=7 + zlib.crc32(name.encode()) % 1000)
     precision = {"fp32": mra.MRA_FP32, "bf16": mra.MRA_BF16_RESCORE, "fp16": mra.MRA_FP16_RESCORE}[prec]
-    _check_poses_and_averages(mra, refs, imgs, O.MRAConfig(L, r1, r2, dr, R, step, mirror), precision=precision)
+    _check_poses_and_averages(mra, refs, imgs, O.MRAConfig(L, r1, r2, dr, R, step, mirror), precision=precision,
+                              kernel=KERNEL_CODE[kernel])
 
 
 def _pose_rows(poses):
@@ -186,12 +199,12 @@ def _pose_rows(poses):
     return rows
 
 
-def _check_poses_and_averages(mra, refs, imgs, cfg, sample=None, precision=None, chunk_images=0):
+def _check_poses_and_averages(mra, refs, imgs, cfg, sample=None, precision=None, chunk_images=0, kernel=0):
     K = refs.shape[0]
     rings = O.ring_table(cfg.first_ring, cfg.last_ring, cfg.ring_step)
     M = O.angle_count(rings)
     al = mra.Aligner(cfg.L, cfg.first_ring, cfg.last_ring, cfg.ring_step, cfg.shift_range, cfg.shift_step,
-                     cfg.mirror, mra.MRA_FP32 if precision is None else precision, chunk_images)
+                     cfg.mirror, mra.MRA_FP32 if precision is None else precision, chunk_images, kernel)
     dimgs = imgs.to(DEV) if not imgs.is_cuda else imgs
     al.set_refs(refs.to(DEV))
     gp = mra.decode_poses(al.align(dimgs))
@@ -241,49 +254,79 @@ def test_workload_n500_L76_K10(mra, prec):
     assert np.mean(gp["k"] == truth.k) > 0.5
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_workload_n100k_L76_K100_sampled(mra, prec):
-    """Full-size 100,000-image, K = 100, 81-shift stack in the benchmark's launch configuration;
-    sampled images against the oracle."""
+def _check_sampled(gp, sample, ops, where):
+    """Poses of the sampled images against the oracle (tolerances of the module docstring); a pose
+    that differs from the oracle's must be a near tie scoring within the tolerance of the best."""
+    ties = 0
+    for i, o in zip(sample, ops):
+        assert abs(gp["cc"][i] - o["cc"]) <= CC_TOL * abs(o["cc"]), (where, i, gp["cc"][i], o["cc"])
+        got = (int(gp["k"][i]), int(gp["shift_idx"][i]), int(gp["mirror"][i]), int(gp["ang_idx"][i]))
+        want = (o["k"], o["shift_idx"], o["mirror"], o["ang_idx"])
+        if o["rel_gap"] > GAP:
+            assert got == want, (where, i, got, want, o["rel_gap"])
+        elif got != want:
+            v = table_value(o, got)
+            assert v is not None and v >= o["cc"] - CC_TOL * abs(o["cc"]), (where, i, got, want, v, o["cc"])
+            ties += 1
+    return ties
+
+
+@pytest.fixture(scope="module")
+def n100k_case():
+    """The 100,000-image, K = 100, 81-shift benchmark stack on the device and the oracle's poses for
+    200 seeded images of it (computed once, in a spawn pool on the host cores)."""
     w = synth.WORKLOADS["mra_n100k_L76_K100_shift4"]
     refs, imgs, truth, _ = synth.make_workload(w, device=DEV)
-    cfg = O.MRAConfig(w.L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror)
-    rng = np.random.default_rng(5 if prec == "fp32" else 6)
-    sample = sorted(set(rng.integers(0, w.n, size=5).tolist()) | {0, w.n - 1})
-    precision = mra.MRA_FP32 if prec == "fp32" else mra.MRA_BF16_RESCORE
-    _check_poses_and_averages(mra, refs, imgs, cfg, sample=sample, precision=precision)
+    cfgd = dict(L=w.L, first_ring=w.first_ring, last_ring=w.last_ring, ring_step=w.ring_step,
+                shift_range=w.shift_range, shift_step=w.shift_step, mirror=w.mirror)
+    rng = np.random.default_rng(2024)
+    sample = sorted(set(rng.choice(w.n, size=198, replace=False).tolist()) | {0, w.n - 1})
+    ops = oracle_poses(imgs[sample].double().cpu().numpy(), refs.double().cpu().numpy(), cfgd)
+    return w, refs, imgs, sample, ops
+
+
+@pytest.mark.parametrize("prec,kernel", [("fp32", "default"), ("bf16", "mma_sync"), ("bf16", "tcgen05"),
+                                         ("fp16", "tcgen05")])
+def test_workload_n100k_L76_K100_sampled(mra, n100k_case, prec, kernel):
+    """Full-size 100,000-image, K = 100, 81-shift stack in the benchmark's launch configuration;
+    200 seeded images (first and last included) against the oracle."""
+    w, refs, imgs, sample, ops = n100k_case
+    precision = {"fp32": mra.MRA_FP32, "bf16": mra.MRA_BF16_RESCORE, "fp16": mra.MRA_FP16_RESCORE}[prec]
+    al = mra.Aligner(w.L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, precision,
+                     kernel=KERNEL_CODE[kernel])
+    al.set_refs(refs)
+    gp = mra.decode_poses(al.align(imgs))
+    al.close()
+    assert len(sample) == 200
+    ties = _check_sampled(gp, sample, ops, (prec, kernel))
+    assert ties <= len(sample) // 10, ties
 
 
 @pytest.fixture(scope="module")
 def l128_case():
-    """The larger-box workload (L = 128, K = 200, rings 1..60, M = 512, 169
-    shifts): 600 images (several chunks and a ragged tail) and the oracle's
-    tables for two of them."""
+    """The larger-box workload (L = 128, K = 200, rings 1..60, M = 512, 169 shifts): 600 images
+    (several chunks and a ragged tail) and the oracle's poses for 64 seeded images of them."""
     w = synth.WORKLOADS["mra_n50k_L128_K200_shift6"]
     refs, imgs, _, _ = synth.make_workload(w, n=600)
-    cfg = O.MRAConfig(w.L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror)
-    spec = O.reference_spectra(refs.double().numpy(), cfg)
-    sample = [0, 599]
-    tabs = {i: O.cc_table(imgs[i].double().numpy(), spec, cfg) for i in sample}
-    return w, refs, imgs, cfg, tabs
+    cfgd = dict(L=w.L, first_ring=w.first_ring, last_ring=w.last_ring, ring_step=w.ring_step,
+                shift_range=w.shift_range, shift_step=w.shift_step, mirror=w.mirror)
+    rng = np.random.default_rng(128)
+    sample = sorted(set(rng.choice(600, size=62, replace=False).tolist()) | {0, 599})
+    ops = oracle_poses(imgs[sample].double().numpy(), refs.double().numpy(), cfgd)
+    return w, refs, imgs, sample, ops
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_workload_L128_K200_sampled(mra, l128_case, prec):
-    w, refs, imgs, cfg, tabs = l128_case
+    w, refs, imgs, sample, ops = l128_case
     precision = {"fp32": mra.MRA_FP32, "bf16": mra.MRA_BF16_RESCORE, "fp16": mra.MRA_FP16_RESCORE}[prec]
     al = mra.Aligner(w.L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, precision)
     al.set_refs(refs.to(DEV))
     gp = mra.decode_poses(al.align(imgs.to(DEV)))
     al.close()
-    for i, tab in tabs.items():
-        p = O._pose_from_table(tab, cfg)
-        assert abs(gp["cc"][i] - p.cc) <= CC_TOL * abs(p.cc), (i, gp["cc"][i], p.cc)
-        got = (int(gp["k"][i]), int(gp["shift_idx"][i]), int(gp["mirror"][i]), int(gp["ang_idx"][i]))
-        if p.rel_gap > GAP:
-            assert got == (p.k, p.shift_idx, p.mirror, p.ang_idx), (i, got, p)
-        else:
-            assert tab[got] >= p.cc - CC_TOL * abs(p.cc)
+    assert len(sample) == 64
+    ties = _check_sampled(gp, sample, ops, prec)
+    assert ties <= len(sample) // 10, ties
 
 
 def test_chunking_and_ragged_tail_match_single_chunk(mra):
@@ -375,8 +418,9 @@ def test_status_codes_and_fault_injection(mra):
     al.close()
 
 
-@pytest.mark.parametrize("prec,L,r2", [("fp32", 32, 12), ("bf16", 32, 12), ("bf16", 76, 35)])
-def test_device_wait_timeout_is_reported_and_recoverable(mra, prec, L, r2):
+@pytest.mark.parametrize("prec,L,r2,kernel", [("fp32", 32, 12, 0), ("bf16", 32, 12, 0), ("bf16", 76, 35, 1),
+                                               ("bf16", 76, 35, 2)])
+def test_device_wait_timeout_is_reported_and_recoverable(mra, prec, L, r2, kernel):
     """A bounded mbarrier wait that gives up sets the device flag; mra_sync reports MRA_ETIMEOUT.
 
     The first wait of every consumer warp is shortened to zero polls (the
@@ -386,7 +430,7 @@ def test_device_wait_timeout_is_reported_and_recoverable(mra, prec, L, r2):
     """
     refs, imgs = _inputs(L, 3, 4, 1.0, 1, seed=31)
     precision = mra.MRA_FP32 if prec == "fp32" else mra.MRA_BF16_RESCORE
-    al = mra.Aligner(L, 1, r2, 1, 1.0, 1.0, 1, precision)
+    al = mra.Aligner(L, 1, r2, 1, 1.0, 1.0, 1, precision, kernel=kernel)
     al.set_refs(refs.to(DEV))
     good = al.align(imgs.to(DEV))
     mra.mra_sync(al.h)

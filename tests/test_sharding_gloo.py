@@ -1,9 +1,11 @@
-"""World-size-2 sharding of the class average on CPU ranks (gloo).
+"""World-size-2 sharding of the class average (gloo).
 
-Each rank takes its contiguous shard, forms its class sums (here with the
-oracle's aligned images, standing in for mra_class_sums, which needs a GPU),
-the product's exchange step sums them over ranks, and the finalised average
-must equal the unsharded oracle average.
+The CPU test covers the partition and the exchange step: each rank takes its
+contiguous shard, forms its class sums with the oracle's aligned images (a
+stand-in for mra_class_sums, which needs a GPU), the product's exchange step
+sums them over ranks, and the finalised average must equal the unsharded
+oracle average.  The GPU test covers the library's half: the ranks form
+their sums with mra_class_sums and finalise with mra_average_finalize.
 """
 import math
 import os
@@ -82,3 +84,75 @@ def test_two_rank_class_average_matches_unsharded():
     for k in range(K):
         if counts[k]:
             np.testing.assert_allclose((sums[k] + comp[k]) / counts[k], avg_ref[k], atol=1e-12)
+
+
+def _gpu_worker(rank, world, port, imgs, refs, poses, cfg, K, out):
+    """One rank: its shard's compensated class sums through the library (mra_class_sums on the GPU),
+    the exchange step over gloo on host copies, and the finalised average (mra_average_finalize)."""
+    import paper_2011_05755_gb300 as mra
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    a, b = shard_range(len(imgs), world, rank)
+    L = imgs.shape[-1]
+    al = mra.Aligner(*cfg)
+    al.set_refs(refs.cuda())  # the class sums need the handle's K
+    sums = torch.zeros((K, L, L), device="cuda")
+    comp = torch.zeros_like(sums)
+    counts = torch.zeros((K,), dtype=torch.int32, device="cuda")
+    if b > a:
+        mra.mra_class_sums(al.h, imgs[a:b].cuda().contiguous(), poses[a:b].cuda().contiguous(), sums, comp, counts)
+    hs, hc, hn = sums.cpu(), comp.cpu(), counts.cpu()
+    allreduce_class_sums(hs, hc, hn)
+    avg = torch.zeros((K, L, L), device="cuda")
+    mra.mra_average_finalize(al.h, hs.cuda(), hc.cuda(), hn.cuda(), avg)
+    if rank == 0:
+        out.put((avg.cpu().numpy(), hn.numpy()))
+    al.close()
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_two_rank_library_class_sums_match_unsharded_average():
+    """The library's half of the exchange: two ranks (processes on the one GPU, whose kernels never wait
+    on each other) form their shards' sums with mra_class_sums, all-reduce them over gloo and finalise;
+    the result equals mra_average of the whole stack within FP32 rounding."""
+    import paper_2011_05755_gb300 as mra
+    import synth
+    import __graft_entry__ as entry
+    entry.build()
+    L, K = 40, 5
+    refs, blob = synth.make_refs(K, L, blobs=8, sigma=(2.0, 4.0), disc=8.0, seed=13)
+    imgs, _ = synth.make_particles(blob, 301, shift_range=2, mirror=True, snr=1.0, seed=14, noise_seed=15)
+    imgs = imgs.float().contiguous()
+    cfg = (L, 1, 16, 1, 2.0, 1.0, 1)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    # poses and the unsharded average in a child too: this process never initialises CUDA
+    procs = [ctx.Process(target=_unsharded_worker, args=(imgs, refs.float().contiguous(), cfg, q))]
+    procs[0].start()
+    poses, want_avg, want_cnt = q.get(timeout=300)
+    procs[0].join(timeout=60)
+    assert procs[0].exitcode == 0
+    port = _free_port()
+    procs = [ctx.Process(target=_gpu_worker, args=(r, 2, port, imgs, refs.float().contiguous(), poses, cfg, K, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    avg, cnt = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert np.array_equal(cnt, want_cnt)
+    np.testing.assert_allclose(avg, want_avg, rtol=0, atol=1e-5)
+
+
+def _unsharded_worker(imgs, refs, cfg, out):
+    import paper_2011_05755_gb300 as mra
+    torch.cuda.set_device(0)
+    al = mra.Aligner(*cfg)
+    al.set_refs(refs.cuda())
+    poses = al.align(imgs.cuda())
+    avg, cnt = al.average(imgs.cuda(), poses)
+    out.put((poses.cpu(), avg.cpu().numpy(), cnt.cpu().numpy()))
+    al.close()
