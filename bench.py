@@ -51,8 +51,10 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="synthetic workload (default: the 100,000-particle bench stack; the others are for "
                          "extra measurements, e.g. mra_n50k_L128_K200_shift6)")
-    ap.add_argument("--serve-requests", type=int, default=60,
-                    help="requests in the serving run (Poisson stream at 0.7 x capacity); 0 skips it")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests in each serving run (Poisson streams at 0.5, 0.7 and 0.9 x capacity); 0 skips it")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the larger-box workload leg (128 px, K = 200, 169 shifts, three precisions)")
     return ap.parse_args()
 
 
@@ -283,16 +285,25 @@ def main():
     rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
     stream = torch.cuda.current_stream()
 
-    def run_path(prec_code, label):
+    def run_path(prec_code, label, w, refs, imgs, n, steps, warmup):
+        K, L = w.K, w.L
+        rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
+        # launch choices of this configuration from the autotuner (timed candidates, cached in JSON)
+        from paper_2011_05755_gb300.autotune import tune
+        choice = tune(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, prec_code, K)
         al = mra.Aligner(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror,
-                         prec_code)
+                         prec_code, choice["chunk_images"], choice["kernel"])
         poses = torch.empty((n, 8), dtype=torch.int32, device=dev)
         avg = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
         counts = torch.zeros((K,), dtype=torch.int32, device=dev)
         sums = torch.zeros((K, L, L), dtype=torch.float32, device=dev)
         comp = torch.zeros_like(sums)
 
-        def step():
+        def step(eager=False):
+            if world == 1 and not eager:
+                # set_refs + align + class average as one CUDA graph launch (captured on the second call)
+                mra.mra_run_graph(al.h, refs, imgs, poses, avg, counts, stream)
+                return
             al.set_refs(refs, stream)
             al.align(imgs, poses, stream)
             if world == 1:
@@ -305,11 +316,11 @@ def main():
                 allreduce_class_sums(sums, comp, counts)
                 mra.mra_average_finalize(al.h, sums, comp, counts, avg, stream)
 
-        for _ in range(args.warmup):
+        for _ in range(max(warmup, 2)):
             step()
         mra.mra_sync(al.h)
         info = al.info
-        mra.mra_profile(al.h, True)
+        graph = world == 1 and mra.mra_graph_info(al.h)
         clocks = ClockSampler(local)
         clocks.start()
         if world > 1:
@@ -318,7 +329,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -327,13 +338,18 @@ def main():
         clk = clocks.stop()
         mra.mra_sync(al.h)
         ms_total = ev0.elapsed_time(ev1)
+        # per-stage device times and kernel launches: one more step, eager, with stage timing on
+        mra.mra_profile(al.h, True)
+        step(eager=True)
+        mra.mra_sync(al.h)
         prof = mra.mra_profile_read(al.h)
         mra.mra_profile(al.h, False)
+        prof_steps = 1
         if world > 1:
             t = torch.tensor([ms_total], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_total = float(t.item())
-        ms_step = ms_total / args.steps
+        ms_step = ms_total / steps
         S = info["S"]
         f_con, f_ifft = path_work(info["M"], rings)
         sm_max = clk.get("sm_max_mhz") or 2070.0
@@ -355,7 +371,7 @@ def main():
         # the contraction / inverse-DFT kernel: one launch per chunk
         cc = prof["cc"]
         launches_cc = max(1, cc["launches"])
-        pairs_per_launch = n * S * K * args.steps / launches_cc
+        pairs_per_launch = n * S * K * prof_steps / launches_cc
         cc_s = cc["ms"] / launches_cc / 1000.0
         if prec_code == mra.MRA_FP32:
             kname = "cc_fp32_kernel"
@@ -364,6 +380,8 @@ def main():
                        "achieved": flops / cc_s / 1e12, "peak": alu_peak, "unit": "TFLOP/s", "peak_source": alu_src}
         else:
             kname = {256: "cc_tc256_kernel", 512: "cc_tc512_kernel"}.get(info["M"], "cc_tc_kernel")
+            if info["M"] == 256 and choice["kernel"] == mra.MRA_KERNEL_TCGEN05:
+                kname = "cc_umma256_kernel"
             flops = pairs_per_launch * (f_con + (f_ifft if info["M"] == 256 else 0))
             cc_line = {"bound": "tensor", "kernel": kname + " (16-bit tensor-core contraction"
                        + (" and inverse angular DFT" if info["M"] == 256 else " + FP32 inverse DFT") + ", row maxima)",
@@ -371,11 +389,11 @@ def main():
         cc_line.update({"frac": cc_line["achieved"] / cc_line["peak"], "traffic": traffic_for(kname, pairs_per_launch),
                         "unit_of_work": "(row, reference) pair", "flop_per_unit": flops / pairs_per_launch,
                         "units_per_launch": pairs_per_launch, "avg_launch_ms": cc_s * 1000.0,
-                        "share_of_step": cc["ms"] / ms_total})
+                        "share_of_step": cc["ms"] / (prof_steps * ms_step)})
         # polar resampling + ring FFT: one launch per chunk (plus one for the references)
         po = prof["polar"]  # particle launches only (the references' launch is the "refs" stage)
         launches_po = max(1, po["launches"])
-        rows_per_launch = n * S * args.steps / launches_po
+        rows_per_launch = n * S * prof_steps / launches_po
         po_s = po["ms"] / launches_po / 1000.0
         f_row = sum(2.5 * nr * math.log2(nr) + 9.0 * nr for _, nr in rings)
         po_line = {"bound": "alu", "kernel": "polar_fft_kernel (bilinear polar resampling + ring FFT)",
@@ -383,7 +401,7 @@ def main():
                    "peak_source": alu_src, "unit_of_work": "(image, shift) row", "flop_per_unit": f_row,
                    "units_per_launch": rows_per_launch, "avg_launch_ms": po_s * 1000.0,
                    "traffic": traffic_for("polar_fft_kernel", rows_per_launch),
-                   "share_of_step": po["ms"] / ms_total}
+                   "share_of_step": po["ms"] / (prof_steps * ms_step)}
         po_line["frac"] = po_line["achieved"] / po_line["peak"]
         roofline, other = (cc_line, po_line) if cc["ms"] >= po["ms"] else (po_line, cc_line)
         roofline = dict(roofline, other_kernel=other)
@@ -413,21 +431,28 @@ def main():
                              "M = 256, inverse-DFT flops at the BF16 peak; FP32: polar rows, FP32 contraction / "
                              "inverse DFT and the 8 rescored rows per image; HBM: stack read twice, spectra "
                              "written and read once, row maxima); frac = the largest / measured step time"}
+        launches_step = sum(v["launches"] for v in prof.values())
         return {"label": label, "al": al, "value": n * world / (ms_step / 1000.0), "ms_step": ms_step,
                 "prof": prof, "roofline": roofline, "clocks": clk, "info": info, "step_roofline": step_roof,
-                "gpu_launches": sum(v["launches"] for v in prof.values())}
+                "gpu_launches": launches_step * steps,
+                "launch": {"graph": bool(graph), "graph_launches_per_step": 1 if graph else 0,
+                           "kernel_launches_per_step": launches_step,
+                           "tuned": {"kernel": {0: "default", 1: "mma.sync", 2: "tcgen05"}[choice["kernel"]],
+                                     "chunk_images": choice["chunk_images"], "chunk_used": info["chunk_images"],
+                                     "candidates": choice["candidates"]}}}
 
     prec_label = args.precision
-    main_res = run_path(prec, prec_label)
+    main_res = run_path(prec, prec_label, w, refs, imgs, n, args.steps, args.warmup)
     cmp_res = None
     if not args.no_compare and prec != mra.MRA_FP32:
-        cmp_res = run_path(mra.MRA_FP32, "fp32")
+        cmp_res = run_path(mra.MRA_FP32, "fp32", w, refs, imgs, n, args.steps, args.warmup)
         cmp_res["al"].close()
     al = main_res["al"]
     value, ms_step, prof, roofline, clk, info = (main_res[k] for k in ("value", "ms_step", "prof", "roofline",
                                                                         "clocks", "info"))
     S = info["S"]
     gpu_launches = main_res["gpu_launches"]
+    launch = main_res["launch"]
 
     # end to end through the host-buffer entry point (pinned memory, copies inside the timed region)
     e2e = None
@@ -454,13 +479,32 @@ def main():
                "d2h_bytes_per_step": h_poses.numel() * 4 + h_avg.numel() * 4 + h_cnt.numel() * 4,
                "ms_per_step": dt * 1000.0, "api": "mra_run_host"}
 
+    # the larger-box workload (128 x 128 px, K = 200, 169 shifts, rings 1..60, M = 512) in all three
+    # precisions: a 10,000-image stack, 3 timed steps each
+    larger_box = None
+    if rank == 0 and world == 1 and not args.no_extra:
+        w3 = synth.WORKLOADS["mra_n50k_L128_K200_shift6"]
+        n3 = 10000
+        refs3, imgs3, _, _ = synth.make_workload(w3, n=n3, device=dev)
+        larger_box = {"workload": w3.name, "n_images": n3, "steps": 3, "warmup": 2,
+                      "note": "the 50,000-image workload's shapes on a 10,000-image stack (images/s does not "
+                              "depend on the stack size once it spans many chunks)"}
+        for pl, pc in (("bf16", mra.MRA_BF16_RESCORE), ("fp16", mra.MRA_FP16_RESCORE), ("fp32", mra.MRA_FP32)):
+            r3 = run_path(pc, pl, w3, refs3, imgs3, n3, 3, 2)
+            larger_box[pl] = {"value": r3["value"], "unit": "images/s", "ms_per_step": r3["ms_step"],
+                              "roofline": r3["roofline"], "clocks": r3["clocks"], "launch": r3["launch"],
+                              "stages": r3["prof"], "gpu_launches": r3["gpu_launches"]}
+            r3["al"].close()
+        del refs3, imgs3
+        torch.cuda.empty_cache()
+
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         from paper_2011_05755_gb300.serve import run_stream
         al.close()  # the stream run holds its own handles
         del imgs
         torch.cuda.empty_cache()
-        serving = run_stream(args.serve_requests, [0.7], prec, calibration_requests=24)
+        serving = run_stream(args.serve_requests, [0.5, 0.7, 0.9], prec, calibration_requests=24)
         serving["precision"] = args.precision
 
     if rank == 0:
@@ -475,14 +519,16 @@ def main():
                                              "fp16": "FP16 contraction + FP32 rescore of top-8 rows"}[args.precision],
                        "step": "set_refs + align + class average",
                        "l2": f"inputs ({n * L * L * 4 / 1e9:.1f} GB/GPU) larger than L2; no flush"},
-            "e2e": e2e, "gpu_launches": gpu_launches, "stages": prof, "roofline": roofline,
-            "cpu_baseline": cpu_line, "clocks": clk, "serving": serving, "step_roofline": main_res["step_roofline"],
+            "e2e": e2e, "gpu_launches": gpu_launches, "launch": launch, "stages": prof, "roofline": roofline,
+            "cpu_baseline": cpu_line, "clocks": clk, "serving": serving, "larger_box": larger_box,
+            "step_roofline": main_res["step_roofline"],
         }
         if cmp_res is not None:
             line["fp32_path"] = {"value": cmp_res["value"], "ms_per_step": cmp_res["ms_step"],
                                  "speedup_of_headline_path": value / cmp_res["value"],
                                  "roofline": cmp_res["roofline"], "stages": cmp_res["prof"],
-                                 "gpu_launches": cmp_res["gpu_launches"], "clocks": cmp_res["clocks"],
+                                 "gpu_launches": cmp_res["gpu_launches"], "launch": cmp_res["launch"],
+                                 "clocks": cmp_res["clocks"],
                                  "step_roofline": cmp_res["step_roofline"]}
         print(json.dumps(line), flush=True)
     al.close()

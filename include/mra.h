@@ -128,9 +128,10 @@ typedef struct {
  * Errors: MRA_EINVAL for a malformed configuration (see mra_config_t);
  * MRA_EUNSUPPORTED, before any CUDA call, when a kernel the configuration
  * launches would need more than 227 KB of shared memory per CTA (the
- * message names it; e.g. the 16-bit paths' FP32 rescore CTA holds one
- * image, its ring samples and its ring spectra, which exceeds the limit
- * from about L = 130 with rings beyond 62); MRA_ECUDA if a CUDA call
+ * message names it; e.g. on the 16-bit paths the polar kernel's CTA holds
+ * the image in a zero border, one row's ring samples and its 16-bit
+ * spectrum words, which exceeds the limit beyond about L = 136 with rings
+ * up to 65 or L = 100 with rings up to 81); MRA_ECUDA if a CUDA call
  * fails. */
 int mra_create(const mra_config_t *cfg, mra_t *out);
 
@@ -216,6 +217,24 @@ int mra_refresh_refs(mra_t h, float *d_refs, const int32_t *d_counts, int32_t K,
  * outputs are in host memory.  Pinned host buffers copy fastest. */
 int mra_run_host(mra_t h, const float *h_refs, int32_t K, const float *h_imgs, int64_t n,
                  mra_pose_t *h_poses, float *h_avg, int32_t *h_counts, mra_stream_t stream);
+
+/* The whole pass of Algorithm 1 on device buffers (the batch pattern: one
+ * launch per pass): mra_set_refs(d_refs, K), mra_align(d_imgs, n, d_poses)
+ * and mra_average(d_imgs, d_poses, n, d_avg, d_counts), run as ONE CUDA graph
+ * launch on `stream`.  The first call with a given set of buffers and sizes
+ * runs the three calls one after the other (sizing and allocating every
+ * workspace); the second captures them into a graph (on a stream of the
+ * handle; nothing runs during the capture) and launches it, and every later
+ * call with the same buffers and sizes replays it.  A call with other buffers or sizes drops
+ * the graph and starts again.  The buffers' contents may change between
+ * calls; their addresses and sizes must not while a graph is cached.
+ * Stage timing (mra_profile) records only the eager calls.  Same errors as
+ * the three calls; MRA_ECUDA if capture or instantiation fails.  No
+ * counterpart in the paper: this is launch plumbing. */
+int mra_run_graph(mra_t h, const float *d_refs, int32_t K, const float *d_imgs, int64_t n, mra_pose_t *d_poses,
+                  float *d_avg, int32_t *d_counts, mra_stream_t stream);
+/* *captured = 1 once mra_run_graph holds an instantiated graph, else 0. */
+int mra_graph_info(mra_t h, int32_t *captured);
 
 /* Wait for the handle's work on `stream`, then report device-side failures:
  * MRA_ETIMEOUT if a kernel gave up a bounded wait for its own asynchronous

@@ -25,7 +25,7 @@ __all__ = [
     "library_path", "load_library", "mra_create", "mra_destroy", "mra_last_error", "mra_get_info",
     "mra_set_refs", "mra_align", "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host",
     "mra_debug_polar", "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync",
-    "mra_align_static", "mra_refresh_refs", "mra_copy_refs", "STAGES",
+    "mra_align_static", "mra_refresh_refs", "mra_copy_refs", "mra_run_graph", "mra_graph_info", "STAGES",
     "Aligner", "decode_poses", "EXPORTED_SYMBOLS",
 ]
 
@@ -39,7 +39,7 @@ EXPORTED_SYMBOLS = [
     "mra_create", "mra_destroy", "mra_last_error", "mra_get_info", "mra_set_refs", "mra_align",
     "mra_average", "mra_class_sums", "mra_average_finalize", "mra_run_host", "mra_debug_polar",
     "mra_debug_spectra", "mra_debug_cc", "mra_profile", "mra_profile_read", "mra_sync", "mra_align_static", "mra_refresh_refs",
-    "mra_copy_refs",
+    "mra_copy_refs", "mra_run_graph", "mra_graph_info",
 ]
 
 STAGES = ("polar", "refs", "cc", "decode", "average", "rescore", "convert", "unused")
@@ -109,6 +109,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "mra_align_static": ([ctypes.POINTER(MRAConfig), vp, i32, vp, i64, vp, vp, ctypes.c_char_p, i32],
                              ctypes.c_int),
         "mra_profile_read": ([vp, ctypes.POINTER(MRAStageTime)], ctypes.c_int),
+        "mra_run_graph": ([vp, vp, i32, vp, i64, vp, vp, vp, vp], ctypes.c_int),
+        "mra_graph_info": ([vp, ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -286,6 +288,27 @@ def mra_align_static(refs: torch.Tensor, imgs: torch.Tensor, poses: torch.Tensor
                                          _dev_ptr(poses, torch.int32, "poses"), _stream(stream), buf, len(buf))
     if rc != MRA_OK:
         raise MRAError(rc, buf.value.decode())
+
+
+def mra_run_graph(h, refs: torch.Tensor, imgs: torch.Tensor, poses: torch.Tensor, avg: torch.Tensor,
+                  counts: torch.Tensor, stream=None) -> None:
+    """set_refs + align + class average as one cached CUDA graph launch (see include/mra.h)."""
+    if imgs.dim() != 3 or refs.dim() != 3 or tuple(refs.shape[1:]) != tuple(imgs.shape[1:]):
+        raise ValueError(f"refs {list(refs.shape)} and imgs {list(imgs.shape)} must be stacks of one box size")
+    _check_poses(poses, imgs.shape[0])
+    if tuple(avg.shape) != tuple(refs.shape) or tuple(counts.shape) != (refs.shape[0],):
+        raise ValueError("avg must match refs and counts must have one entry per reference")
+    _check(load_library().mra_run_graph(h, _dev_ptr(refs, torch.float32, "refs"), refs.shape[0],
+                                        _dev_ptr(imgs, torch.float32, "imgs"), imgs.shape[0],
+                                        _dev_ptr(poses, torch.int32, "poses"), _dev_ptr(avg, torch.float32, "avg"),
+                                        _dev_ptr(counts, torch.int32, "counts"), _stream(stream)), h)
+
+
+def mra_graph_info(h) -> bool:
+    """True once mra_run_graph holds an instantiated graph for the handle."""
+    v = ctypes.c_int32()
+    _check(load_library().mra_graph_info(h, ctypes.byref(v)), h)
+    return bool(v.value)
 
 
 def mra_profile(h, enable: bool) -> None:

@@ -29,8 +29,10 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
   float2 *twf = reinterpret_cast<float2 *>(im + LLp);
   float2 *twi = twf + M;
   float2 *Z = twi + M;
-  float2 *spec = Z + IfftShape<M>::P;
-  float *samp = reinterpret_cast<float *>(spec + ((g.NBIN + 1) & ~1));
+  // ring samples, then (in place) each ring's spectrum: N real samples are
+  // transformed as N/2 complex values and split into the bins X(0..N/2) in the
+  // same N floats, with the two real bins packed as (X(0), X(N/2)) in slot 0
+  float *samp = reinterpret_cast<float *>(Z + IfftShape<M>::P);
   int4 *s_rings = reinterpret_cast<int4 *>((reinterpret_cast<uintptr_t>(samp + g.NS) + 15) & ~uintptr_t(15));  // [NR]
   const float c0 = 0.5f * static_cast<float>(L);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -62,8 +64,20 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
       const int N = rd.x, H = N >> 1;
       float2 *z = reinterpret_cast<float2 *>(samp + rd.y);
       warp_fft_inplace(z, H, rd.w, M, twf, lane);
+      __syncwarp();
+      // in-place split: lane pair {kx, H - kx} reads and writes only its two slots
       const int wstep = M / N;
-      for (int kx = lane; kx <= H; kx += 32) spec[rd.z + kx] = real_split(z, H, kx, twf[kx * wstep]);
+      for (int kx = lane; kx <= H / 2; kx += 32) {
+        if (kx == 0) {
+          const float2 x0 = real_split(z, H, 0, twf[0]), xh = real_split(z, H, H, twf[H * wstep]);
+          z[0] = make_float2(x0.x, xh.x);  // both bins are real
+        } else {
+          const float2 xa = real_split(z, H, kx, twf[kx * wstep]);
+          const float2 xb = real_split(z, H, H - kx, twf[(H - kx) * wstep]);
+          z[kx] = xa;
+          z[H - kx] = xb;
+        }
+      }
       __syncwarp();
     }
     __syncthreads();
@@ -87,7 +101,10 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
         const float2 *Bf = Bk + static_cast<int64_t>(g.kpos[f]) * kTile;  // bin (ring, f) at kpos[f] + ring
 #pragma unroll 4
         for (int ring = NR - 1 - half; ring >= lo; ring -= 2) {
-          const float2 A = spec[s_rings[ring].z + f];
+          const int4 rd = s_rings[ring];
+          const float2 *zr = reinterpret_cast<const float2 *>(samp + rd.y);
+          const float2 z0 = zr[0];
+          const float2 A = f == 0 ? make_float2(z0.x, 0.f) : (2 * f == rd.x ? make_float2(z0.y, 0.f) : zr[f]);
           const float2 Bv = __ldg(Bf + static_cast<int64_t>(ring) * kTile);
           p1 = fmaf(A.x, Bv.x, p1);
           p2 = fmaf(A.y, Bv.y, p2);
@@ -141,8 +158,7 @@ size_t rescore_smem(const Geometry &g) {
   const int T = g.M >= 256 ? 16 : g.M / 16;
   const int P = T * (g.M / T + 1);
   return static_cast<size_t>((g.L * g.L + 3) & ~3) * sizeof(float) + (2 * g.M + P) * sizeof(float2) +
-         static_cast<size_t>((g.NBIN + 1) & ~1) * sizeof(float2) + static_cast<size_t>(g.NS) * sizeof(float) + 16 +
-         static_cast<size_t>(g.NR) * sizeof(int4);
+         static_cast<size_t>(g.NS) * sizeof(float) + 16 + static_cast<size_t>(g.NR) * sizeof(int4);
 }
 
 template <int M>

@@ -81,6 +81,21 @@ struct mra_handle {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t workspace = 0;
   std::string err;
+  // whole-pass CUDA graph (mra_run_graph): the buffers and sizes it was captured for
+  struct GraphKey {
+    const void *refs, *imgs, *poses, *avg, *counts;
+    int64_t n;
+    int K;
+    bool operator==(const GraphKey &o) const {
+      return refs == o.refs && imgs == o.imgs && poses == o.poses && avg == o.avg && counts == o.counts && n == o.n &&
+             K == o.K;
+    }
+  };
+  GraphKey graph_key{};
+  int graph_seen = 0;               // calls with graph_key so far (the graph is captured on the second)
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  bool capturing = false;           // stage timing records are not taken inside a capture
   // per-stage event timing (mra_profile)
   bool prof_on = false;
   struct ProfRec {
@@ -129,7 +144,7 @@ cudaEvent_t prof_event(mra_handle *h) {
 
 // Open a timed stage on stream st; returns a record index or -1 when off.
 int prof_begin(mra_handle *h, int stage, cudaStream_t st) {
-  if (!h->prof_on) return -1;
+  if (!h->prof_on || h->capturing) return -1;
   cudaEvent_t a = prof_event(h), b = prof_event(h);
   if (!a || !b) return -1;
   cudaEventRecord(a, st);
@@ -781,6 +796,8 @@ void free_all(mra_handle *h) {
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   for (auto &r : h->prof_recs) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -1247,6 +1264,69 @@ int mra_run_host(mra_t h, const float *h_refs, int32_t K, const float *h_imgs, i
   if ((e = cudaMemcpyAsync(h_counts, h->h_stage_counts, sizeof(int) * K, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_err(h, e, "copy counts out");
   return mra_sync(h, stream);
+}
+
+int mra_run_graph(mra_t h, const float *d_refs, int32_t K, const float *d_imgs, int64_t n, mra_pose_t *d_poses,
+                  float *d_avg, int32_t *d_counts, mra_stream_t stream) {
+  if (int rc = need_handle(h)) return rc;
+  if (K < 1 || n < 1) return set_err(h, MRA_EINVAL, "need K >= 1 and n >= 1");
+  if (!d_refs || !d_imgs || !d_poses || !d_avg || !d_counts) return set_err(h, MRA_EINVAL, "NULL buffer");
+  if (int rc = select_device(h)) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const mra_handle::GraphKey key{d_refs, d_imgs, d_poses, d_avg, d_counts, n, K};
+  auto eager = [&]() -> int {
+    if (int rc = mra_set_refs(h, d_refs, K, stream)) return rc;
+    if (int rc = mra_align(h, d_imgs, n, d_poses, stream)) return rc;
+    return mra_average(h, d_imgs, d_poses, n, d_avg, d_counts, stream);
+  };
+  if (!(key == h->graph_key)) {  // new buffers or sizes: drop the old graph, run eagerly
+    if (h->graph_exec) {
+      cudaGraphExecDestroy(h->graph_exec);
+      h->graph_exec = nullptr;
+    }
+    h->graph_key = key;
+    h->graph_seen = 0;
+  }
+  // the first call with these buffers runs eagerly: it sizes and allocates every workspace and sets
+  // every kernel attribute, none of which may happen inside a capture
+  if (!h->graph_exec && h->graph_seen++ == 0) return eager();
+  if (!h->graph_exec) {
+    cudaError_t e;
+    if (!h->capture_stream &&
+        (e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_err(h, e, "cudaStreamCreate(capture)");
+    if ((e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_err(h, e, "cudaStreamBeginCapture");
+    h->capturing = true;
+    const mra_stream_t cs = reinterpret_cast<mra_stream_t>(h->capture_stream);
+    int rc = mra_set_refs(h, d_refs, K, cs);
+    if (!rc) rc = mra_align(h, d_imgs, n, d_poses, cs);
+    if (!rc) rc = mra_average(h, d_imgs, d_poses, n, d_avg, d_counts, cs);
+    h->capturing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->graph_exec = nullptr;
+      return cuda_err(h, e, "cudaGraphInstantiate");
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(h->graph_exec, st);
+  return e == cudaSuccess ? MRA_OK : cuda_err(h, e, "cudaGraphLaunch");
+}
+
+int mra_graph_info(mra_t h, int32_t *captured) {
+  if (int rc = need_handle(h)) return rc;
+  if (!captured) return set_err(h, MRA_EINVAL, "captured is NULL");
+  *captured = h->graph_exec ? 1 : 0;
+  return MRA_OK;
 }
 
 int mra_sync(mra_t h, mra_stream_t stream) {

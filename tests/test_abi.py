@@ -72,20 +72,21 @@ def test_null_handle_calls_fail_cleanly(lib):
 
 @pytest.mark.parametrize("precision", [mra.MRA_BF16_RESCORE, mra.MRA_FP16_RESCORE])
 def test_create_rejects_configs_beyond_shared_memory(lib, precision):
-    # L = 132 with rings 1..65: the FP32 rescore CTA of the 16-bit paths would
-    # need about 240 KB of shared memory (the image, the ring samples and the
-    # ring spectra of one row); the FP32 path fits and passes the check
+    # L = 192 with rings 1..81: the polar kernel's CTA (the image in its zero
+    # border, a row's ring samples and its 16-bit spectrum words) would need
+    # about 350 KB of shared memory; the rescore CTA (image and ring samples,
+    # spectra in place) would need about 260 KB
     with pytest.raises(mra.MRAError) as ei:
-        mra.mra_create(L=132, first_ring=1, last_ring=65, shift_range=1.0, shift_step=1.0, precision=precision)
+        mra.mra_create(L=192, first_ring=1, last_ring=81, shift_range=1.0, shift_step=1.0, precision=precision)
     assert ei.value.code == mra.MRA_EUNSUPPORTED
-    assert "FP32 rescore" in str(ei.value) and "shared memory" in str(ei.value)
+    assert "kernel would need" in str(ei.value) and "shared memory" in str(ei.value)
 
 
 # Every configuration the GPU tests, the bench and the tools create.
 _USED = [
     (76, 1, 35, 1, 4.0, 1.0), (76, 1, 35, 1, 2.0, 1.0), (76, 1, 35, 1, 3.0, 1.0),   # L = 76 workloads
     (128, 1, 60, 1, 6.0, 1.0), (128, 1, 60, 1, 1.0, 1.0),                            # L = 128 workload, parity case
-    (132, 1, 65, 1, 1.0, 1.0),                                                       # FP32 only at 16-bit limits
+    (132, 1, 65, 1, 1.0, 1.0),                                                       # rings beyond 64 at L = 132
     (90, 1, 36, 1, 6.0, 1.0), (90, 1, 36, 1, 1.0, 1.0),                              # RFA sweep
     (64, 1, 28, 1, 3.0, 1.0), (96, 1, 44, 1, 3.0, 1.0), (128, 1, 60, 1, 3.0, 1.0),   # serving boxes
     (32, 1, 12, 1, 1.5, 0.5), (48, 2, 20, 2, 2.0, 1.0), (24, 1, 15, 1, 2.0, 1.0),    # parity cases
@@ -99,8 +100,6 @@ _USED = [
 @pytest.mark.parametrize("cfg", _USED)
 def test_used_configs_pass_the_shared_memory_check(lib, cfg, precision):
     L, r1, r2, dr, R, step = cfg
-    if L == 132 and precision != mra.MRA_FP32:
-        pytest.skip("beyond the 16-bit paths' shared memory (checked above)")
     try:
         h = mra.mra_create(L=L, first_ring=r1, last_ring=r2, ring_step=dr, shift_range=R, shift_step=step,
                            precision=precision)

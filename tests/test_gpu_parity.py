@@ -50,10 +50,7 @@ CASES = {
     # M = 256 with sparse rings (3, 6, ..., 24: other R_f and frequency groups) and K not a tile multiple
     "M256_r24_step": (56, 3, 24, 3, 1.0, 1.0, 1, 13, 3),
     "M256_nomirror": (64, 2, 30, 1, 2.0, 1.0, 0, 9, 3),
-}
-# FP32 only: rings beyond 64 at L = 132 exceed the shared memory of the
-# 16-bit paths' rescore CTA (mra_create reports MRA_EUNSUPPORTED for them)
-FP32_ONLY_CASES = {
+    # rings beyond 64 at L = 132 (the 16-bit paths' FP32 rescore keeps each ring's spectrum in its samples)
     "M512_r65": (132, 1, 65, 1, 1.0, 1.0, 1, 3, 2),
 }
 
@@ -86,9 +83,9 @@ def _cs_scale(imgs, refs, cfg):
     return np.stack(out)
 
 
-@pytest.mark.parametrize("name", list(CASES) + list(FP32_ONLY_CASES))
+@pytest.mark.parametrize("name", list(CASES))
 def test_stage_parity(mra, name):
-    L, r1, r2, dr, R, step, mirror, K, n = {**CASES, **FP32_ONLY_CASES}[name]
+    L, r1, r2, dr, R, step, mirror, K, n = CASES[name]
     refs, imgs = _inputs(L, K, n, R, mirror, seed=zlib.crc32(name.encode()) % 1000)
     cfg = O.MRAConfig(L, r1, r2, dr, R, step, mirror)
     rings = O.ring_table(r1, r2, dr)
@@ -152,7 +149,8 @@ def tc_tol(prec, M):
 
 
 KERNEL_CODE = {"default": 0, "mma_sync": 1, "tcgen05": 2}
-TC_CASES = [(name, "default") for name in ["M128_ragged", "M128_step2_nomirror", "M512_L128", "M16", "M64"]] + \
+TC_CASES = [(name, "default") for name in ["M128_ragged", "M128_step2_nomirror", "M512_L128", "M512_r65", "M16",
+                                             "M64"]] + \
     [("M256_L76", "mma_sync"), ("M256_L76", "tcgen05"), ("M256_r24_step", "tcgen05"), ("M256_nomirror", "tcgen05")]
 
 
