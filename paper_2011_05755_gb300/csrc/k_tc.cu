@@ -158,22 +158,19 @@ __device__ __forceinline__ void tc_lane_init(TcLane &L, const float2 *tw, int la
     }
 }
 
-// Inverse angular DFT of one pair (M = 256 = 16 x 16) on tensor cores by one
-// warp: Y(k, t) = sum_a w16^(a k) Z(t + 16 a) as a 32 x 32 x 16 real GEMM
-// (A = the DFT matrix [[C, -S], [S, C]], B = Z), twiddle w256^(t k) in FP32,
-// then c(k + 16 j) = sum_t w16^(t j) Y'(k, t) as a 16 x 32 x 32 real GEMM
-// whose A fragments are exactly the stage-1 accumulators.  BF16 operands,
-// FP32 accumulation.  Returns this lane's maxima of the real (unmirrored)
-// and imaginary (mirrored) parts (the caller reduces over the warp); `dbg`
-// (or null) receives every value: dbg[j] = Re c(j),
-// dbg[M + (j + M/2) mod M] = Im c(j).
-__device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, const TcLane &L,
-                                                const uint32_t (&a1)[16], const uint32_t (&b2)[16], int lane,
-                                                float &vu, float &vm, float *dbg) {
-  const int g = lane >> 2, t4 = lane & 3;
-  uint32_t z[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) z[e] = zp[L.zoff[e] ^ sw];
+// 256-point inverse DFT of one pair on tensor cores by one warp (16 x 16):
+// Y(k, t) = sum_a w16^(a k) Z(t + 16 a) as a 32 x 32 x 16 real GEMM (A = the
+// DFT matrix [[C, -S], [S, C]], B = Z), twiddle w256^(t k) in FP32, then
+// c(k + 16 j) = sum_t w16^(t j) Y'(k, t) as a 16 x 32 x 32 real GEMM whose A
+// fragments are exactly the stage-1 accumulators.  BF16 operands, FP32
+// accumulation.  z[nb * 4 + i] is the spectrum word (Re, Im) of
+// f = 8 nb + g + 16 a_i, a_i in {2 t4, 2 t4 + 1, 2 t4 + 8, 2 t4 + 9}, and
+// tw[nb * 4 + q] the stage twiddle w256^(t k) of fragment q of t block nb.
+// On return d2[b][q] (b = 0, 1: real part, b = 2, 3: imaginary part) is c at
+// angle k + 16 j with k = g + 8 (q >> 1), j = 8 (b & 1) + 2 t4 + (q & 1).
+__device__ __forceinline__ void idft256_core(const uint32_t (&z)[8], const float2 (&tw)[8],
+                                             const uint32_t (&a1)[16], const uint32_t (&b2)[16],
+                                             float (&d2)[4][4]) {
   // B fragments: [re/im k-step][t block]; word halves are (Re, Im) of one f
   uint2 b1[2][2];
 #pragma unroll
@@ -200,7 +197,7 @@ __device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, cons
   for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float2 w = L.tw[nb * 4 + q];
+      const float2 w = tw[nb * 4 + q];
       const float r = d1[0][nb][q], im = d1[1][nb][q];
       yr[nb][q] = fmaf(r, w.x, -im * w.y);
       yi[nb][q] = fmaf(r, w.y, im * w.x);
@@ -210,7 +207,6 @@ __device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, cons
                      pack_bf2(yr[1][2], yr[1][3]));
   a2[1] = make_uint4(pack_bf2(yi[0][0], yi[0][1]), pack_bf2(yi[0][2], yi[0][3]), pack_bf2(yi[1][0], yi[1][1]),
                      pack_bf2(yi[1][2], yi[1][3]));
-  float d2[4][4];  // [(re/im of c, j block)][fragment]
 #pragma unroll
   for (int nb = 0; nb < 4; ++nb) {
     d2[nb][0] = d2[nb][1] = d2[nb][2] = d2[nb][3] = 0.f;
@@ -218,6 +214,21 @@ __device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, cons
     for (int ks = 0; ks < 2; ++ks)
       mma16816<false>(d2[nb], a2[ks], make_uint2(b2[(ks * 4 + nb) * 2], b2[(ks * 4 + nb) * 2 + 1]));
   }
+}
+
+// Inverse angular DFT of one pair (M = 256) by one warp (idft256_core).
+// Returns this lane's maxima of the real (unmirrored) and imaginary
+// (mirrored) parts (the caller reduces over the warp); `dbg` (or null)
+// receives every value: dbg[j] = Re c(j), dbg[M + (j + M/2) mod M] = Im c(j).
+__device__ __forceinline__ void pair_idft_tc256(const uint32_t *zp, int sw, const TcLane &L,
+                                                const uint32_t (&a1)[16], const uint32_t (&b2)[16], int lane,
+                                                float &vu, float &vm, float *dbg) {
+  const int g = lane >> 2, t4 = lane & 3;
+  uint32_t z[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) z[e] = zp[L.zoff[e] ^ sw];
+  float d2[4][4];  // [(re/im of c, j block)][fragment]
+  idft256_core(z, L.tw, a1, b2, d2);
   vu = fmaxf(fmaxf(fmaxf(d2[0][0], d2[0][1]), fmaxf(d2[0][2], d2[0][3])),
              fmaxf(fmaxf(d2[1][0], d2[1][1]), fmaxf(d2[1][2], d2[1][3])));
   vm = fmaxf(fmaxf(fmaxf(d2[2][0], d2[2][1]), fmaxf(d2[2][2], d2[2][3])),
@@ -415,28 +426,25 @@ __global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, 
 // M = 512 kernel (rings up to 81): the tile walk and chunked staging of the
 // M = 256 kernel with one CTA of 16 warps per SM (the BF16 spectra of the
 // 64 pairs take 128 KB) and chunks of up to kTc512ChunkKs k-steps.
-// Spectrum word of Z(f) in a pair's 512-word buffer: f ^ s with
+// Spectrum word of Z(f) in a pair's 512-word buffer: z512_fold(f) ^ s with
 // s = 4 (pair / 8) + (pair % 4) < 32, so the contraction's stores (32 lanes,
-// 32 pairs, one f) hit distinct banks.  Phase 2: a half-warp per pair (rows
-// i and i + 4 of one reference in the two halves of a warp), FP32 inverse DFT
-// from the BF16 spectrum in the factorisation 512 = 16 x 32: thread t loads
-// Z(t + 16 a), a = 0..31, runs a length-32 register DFT, applies
-// exp(2 pi i t k / 512), writes its row of the 16 x 32 intermediate back
-// into the pair's buffer as BF16 words (row t, word k ^ lane), and finishes
-// with length-16 DFTs over the columns k = t and t + 16.  All these shared
-// accesses are bank-conflict free: the two half-warps always use opposite
-// halves of the banks.
+// 32 pairs, one f) hit distinct banks.  Phase 2: the inverse DFT on tensor
+// cores by an even / odd split (decimation in frequency index):
+//     c(n)       = E(n) + w512^n O(n),    c(n + 256) = E(n) - w512^n O(n),
+//     E(n) = sum_m Z(2 m) w256^(m n),     O(n) = sum_m Z(2 m + 1) w256^(m n),
+// n = 0..255: two 256-point inverse DFTs per pair (idft256_core) and a
+// radix-2 combine in FP32, one warp per pair.  z512_fold places the words
+// those 256-point DFTs load (f = 2 (8 nb + g + 16 a) (+1)) in 32 distinct
+// banks for every load of the warp.
+__device__ __forceinline__ int z512_fold(int f) { return f ^ ((f >> 6) & 1) ^ (((f >> 7) & 1) << 4); }
+
 constexpr int kTc512Warps = 16;
 constexpr int kTc512Threads = 32 * kTc512Warps;
 constexpr int kTc512MaxChunks = 48;
 constexpr size_t kTc512Stage = static_cast<size_t>(kTc512ChunkKs) * 1024;
-constexpr size_t kTc512Smem = 2 * kTc512Stage + 64 * 512 * sizeof(uint32_t) + 512 * sizeof(float2) +
-                              2 * sizeof(uint64_t) + 8 * sizeof(int2) + (258 + kTc512MaxChunks + 2) * sizeof(int);
+constexpr size_t kTc512Smem = 2 * kTc512Stage + 64 * 512 * sizeof(uint32_t) + 2 * sizeof(uint64_t) + 8 * sizeof(int2) +
+                              (258 + kTc512MaxChunks + 2) * sizeof(int);
 static_assert(kTc512Smem <= 232448, "M = 512 kernel exceeds 227 KB of shared memory");
-
-__device__ __forceinline__ float2 unpack_bf2(uint32_t w) {
-  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
 
 template <bool FP16>
 __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, TcArgs a, int ref_tiles) {
@@ -444,8 +452,7 @@ __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, 
   extern __shared__ float4 smem_f4[];
   unsigned char *stage = reinterpret_cast<unsigned char *>(smem_f4);
   uint32_t *Zw = reinterpret_cast<uint32_t *>(stage + 2 * kTc512Stage);  // [64 pairs][512 words]
-  float2 *tw = reinterpret_cast<float2 *>(Zw + PAIRS * M);
-  uint64_t *full = reinterpret_cast<uint64_t *>(tw + M);
+  uint64_t *full = reinterpret_cast<uint64_t *>(Zw + PAIRS * M);
   int2 *rinfo = reinterpret_cast<int2 *>(full + 2);  // {image, shift} of the tile's rows
   int *s_kso = reinterpret_cast<int *>(rinfo + 8);   // [NF + 1]
   int *s_cf = s_kso + NF + 1;                        // [NCH + 1]
@@ -454,7 +461,6 @@ __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nch = g.NCH;
   const int total = ref_tiles * nch;
-  for (int i = tid; i < M; i += kTc512Threads) tw[i] = g.inv_tw[i];
   for (int i = tid; i <= NF; i += kTc512Threads) s_kso[i] = g.kso[i];
   for (int i = tid; i <= nch; i += kTc512Threads) s_cf[i] = g.chunk_f[i];
   if (tid < 8) {
@@ -491,7 +497,46 @@ __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, 
   uint32_t *z0 = Zw + (8 * g8 + t4) * M;   // pair (row g8, reference t4)
   uint32_t *z1 = z0 + 4 * M;               // pair (row g8, reference 4 + t4)
   const int S = g.S;
-  const int hw = lane >> 4, t = lane & 15;  // phase 2: half-warp, thread within the pair's group
+
+  // lane constants of phase 2: the 16-point DFT fragments, the folded word
+  // positions of the even spectrum words this lane loads (the odd word of
+  // each sits at the position XOR 1), the 256-point stage twiddles
+  // w256^(t k) = w512^(2 t k) and the combine twiddles w512^n of its angles
+  // (g.angles[q] = exp(2 pi i q / M))
+  uint32_t a1[16], b2[16];
+  {
+    const uint4 *fa = reinterpret_cast<const uint4 *>(g.dft16) + lane * 4;
+    const uint4 *fb = reinterpret_cast<const uint4 *>(g.dft16 + 512) + lane * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint4 va = __ldg(fa + i), vb = __ldg(fb + i);
+      a1[4 * i] = va.x;
+      a1[4 * i + 1] = va.y;
+      a1[4 * i + 2] = va.z;
+      a1[4 * i + 3] = va.w;
+      b2[4 * i] = vb.x;
+      b2[4 * i + 1] = vb.y;
+      b2[4 * i + 2] = vb.z;
+      b2[4 * i + 3] = vb.w;
+    }
+  }
+  int zoff[8];
+  float2 tws[8], wn[8];
+  {
+    const int aa[4] = {2 * t4, 2 * t4 + 1, 2 * t4 + 8, 2 * t4 + 9};
+#pragma unroll
+    for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) zoff[nb * 4 + e] = z512_fold(2 * (8 * nb + g8 + 16 * aa[e]));
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = g8 + 8 * (q >> 1);
+        tws[b * 4 + q] = __ldg(g.angles + ((2 * (8 * b + 2 * t4 + (q & 1)) * k) & (M - 1)));
+        wn[b * 4 + q] = __ldg(g.angles + k + 16 * (8 * b + 2 * t4 + (q & 1)));
+      }
+  }
 
   int q = 0;  // global chunk index
   for (int kt = 0; kt < ref_tiles; ++kt) {
@@ -521,11 +566,11 @@ __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, 
             }
           }
           // lane (g8, t4): d[0..1] = Re/Im Z(f), d[2..3] = Im/Re Z(M - f)
-          const int pf = f ^ sw;
+          const int pf = z512_fold(f) ^ sw;
           z0[pf] = pack_bf2(d0[0], d0[1]);
           z1[pf] = pack_bf2(d1[0], d1[1]);
           if (f != 0 && f != M / 2) {
-            const int pm = (M - f) ^ sw;
+            const int pm = z512_fold(M - f) ^ sw;
             z0[pm] = pack_bf2(d0[3], d0[2]);
             z1[pm] = pack_bf2(d1[3], d1[2]);
           }
@@ -544,66 +589,56 @@ __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, 
       if (tid == 0 && q + 2 < total) issue(q + 2);
     }
 
-    // ---------------- Phase 2: FP32 inverse DFT from the BF16 spectra, row maxima ----------------
+    // ---------------- Phase 2: tensor-core inverse DFT (even / odd split), row maxima ----------------
+    // warp w: reference w % 8 of the tile, rows 4 (w / 8) .. 4 (w / 8) + 3
     const int refl = warp & 7;
     const int ref = kt * 8 + refl;
-    if (ref < a.K) {  // warp-uniform: padding references are skipped
+    const int i0 = 4 * (warp >> 3);
+    const int64_t left = a.rows - rt * 8 - i0;
+    const int nvalid = ref < a.K ? (left >= 4 ? 4 : (left > 0 ? static_cast<int>(left) : 0)) : 0;
 #pragma unroll 1
-      for (int r = 0; r < 2; ++r) {
-        const int i = 2 * (warp >> 3) + r + 4 * hw;  // row of this half-warp's pair
-        uint32_t *zp = Zw + (8 * i + refl) * M;
-        const int s = 4 * i + (refl & 3);            // spectrum swizzle of the pair
-        // Z(t + 16 a) sits at (t ^ (s & 15)) + 16 (a ^ (s >> 4))
-        const uint32_t *ze = zp + (t ^ (s & 15)) + 16 * (s >> 4);  // even a
-        const uint32_t *zo = zp + (t ^ (s & 15)) - 16 * (s >> 4);  // odd a
-        float2 x[32];
+    for (int r = 0; r < nvalid; ++r) {  // padding pairs are skipped (warp-uniform)
+      const int i = i0 + r, pc = 8 * i + refl;
+      const uint32_t *zp = Zw + pc * M;
+      const int swp = 4 * (pc >> 3) + (pc & 3);
+      float de[4][4], dd[4][4];  // E and O at this lane's angles (idft256_core's fragment order)
+      {
+        uint32_t z[8];
 #pragma unroll
-        for (int aa = 0; aa < 32; ++aa) x[aa] = unpack_bf2((aa & 1 ? zo : ze)[16 * aa]);
-        reg_fft<32, +1>(x);
-#pragma unroll
-        for (int k = 1; k < 32; ++k) x[k] = cmul(x[k], tw[k * 16 + t]);
-        __syncwarp();  // every spectrum word of both pairs has been read
-        uint32_t *rowp = zp + 32 * t;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) rowp[k ^ lane] = pack_bf2(x[k].x, x[k].y);
-        __syncwarp();
-        float2 y[2][16];
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const int lk = lane ^ (16 * kk);  // column k = t + 16 kk of row tt sits at word k ^ tt ^ 16 hw
-#pragma unroll
-          for (int tt = 0; tt < 16; ++tt) y[kk][tt] = unpack_bf2(zp[32 * tt + (lk ^ tt)]);
-          reg_fft<16, +1>(y[kk]);  // y[kk][jj] = c(t + 16 kk + 32 jj)
-        }
-        float vu = -INFINITY, vm = -INFINITY;
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            vu = fmaxf(vu, y[kk][jj].x);
-            vm = fmaxf(vm, y[kk][jj].y);
-          }
-        // maxima over the half-warp: threads t < 8 end with max(vu), t >= 8 with max(vm)
-        const bool hi8 = (t & 8) != 0;
-        float v = fmaxf(hi8 ? vm : vu, __shfl_xor_sync(0xffffffffu, hi8 ? vu : vm, 8));
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        const bool valid = rt * 8 + i < a.rows;
-        const int2 ri = rinfo[i];
-        const int64_t rbase = (static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y;
-        if (valid && (t & 7) == 0) a.rowmax[rbase * 2 + (t >> 3)] = (hi8 && !g.mirror) ? -INFINITY : v;
-        if (a.dbg_cc && valid) {
-          float *d = a.dbg_cc + rbase * 2 * M;
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) {
-              const int j = t + 16 * kk + 32 * jj;
-              d[j] = y[kk][jj].x;
-              d[M + ((j + M / 2) & (M - 1))] = y[kk][jj].y;
-            }
-        }
+        for (int e = 0; e < 8; ++e) z[e] = zp[zoff[e] ^ swp];
+        idft256_core(z, tws, a1, b2, de);
       }
+      {
+        uint32_t z[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) z[e] = zp[zoff[e] ^ 1 ^ swp];
+        idft256_core(z, tws, a1, b2, dd);
+      }
+      const int2 ri = rinfo[i];
+      const int64_t rbase = (static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y;
+      float *dbg = a.dbg_cc ? a.dbg_cc + rbase * 2 * M : nullptr;
+      float vu = -INFINITY, vm = -INFINITY;
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 w = wn[b * 4 + q];
+          const float orr = dd[b][q], oi = dd[b + 2][q];
+          const float wr = fmaf(w.x, orr, -w.y * oi), wi = fmaf(w.x, oi, w.y * orr);
+          const float c1r = de[b][q] + wr, c1i = de[b + 2][q] + wi;  // angle n
+          const float c2r = de[b][q] - wr, c2i = de[b + 2][q] - wi;  // angle n + 256
+          vu = fmaxf(vu, fmaxf(c1r, c2r));
+          vm = fmaxf(vm, fmaxf(c1i, c2i));
+          if (dbg) {
+            const int n = g8 + 8 * (q >> 1) + 16 * (8 * b + 2 * t4 + (q & 1));
+            dbg[n] = c1r;
+            dbg[n + 256] = c2r;
+            dbg[M + n + 256] = c1i;  // Im c(n) at (n + M / 2) mod M
+            dbg[M + n] = c2i;        // Im c(n + 256) at n
+          }
+        }
+      const float best = warp_max2(vu, vm, lane);
+      if ((lane & 15) == 0) a.rowmax[rbase * 2 + (lane >> 4)] = (lane && !g.mirror) ? -INFINITY : best;
     }
     __syncthreads();  // the next tile's contraction overwrites the pair buffers
   }

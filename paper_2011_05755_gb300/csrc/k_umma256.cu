@@ -64,7 +64,7 @@ constexpr int kThreads = 64 + 32 * kDrainWarps;
 // the most warps bounds the per-thread count.
 constexpr int kMaxRegs = 96;
 static_assert((kThreads / 32 + 3) / 4 * 32 * kMaxRegs <= 16384, "register file of a sub-partition exceeded");
-constexpr int kUPerStage = 5;                               // k-steps per TMA stage
+constexpr int kUPerStage = kUmmaUPerStage;                  // k-steps per TMA stage (one box per operand)
 constexpr int kStages = 3;
 constexpr uint32_t kABytes = 4096, kBBytes = 2048;          // one k-step: A 128 x 16, B 64 x 16 (BF16/FP16)
 constexpr uint32_t kStageBytes = kUPerStage * (kABytes + kBBytes);
@@ -174,16 +174,15 @@ __global__ void __maxnreg__(u256::kMaxRegs)
               break;
             }
           }
+          // one box of kUPerStage k-steps per operand; a tile's last stage may
+          // read k-steps of the next tile (or zeros past the end), never used
           const int rs = c % kStages;
-          const int n = min(kUPerStage, NU - u0);
           unsigned char *dst = smem + kOffStage + rs * kStageBytes;
-          mbar_arrive_expect_tx(full + rs, static_cast<uint32_t>(n) * (kABytes + kBBytes));
-          for (int i = 0; i < n; ++i) {
-            tma_load_2d(dst + i * kABytes, &tmA, 0, ya, full + rs);
-            tma_load_2d(dst + kUPerStage * kABytes + i * kBBytes, &tmB, 0, yb, full + rs);
-            ya += 16;
-            yb += 8;
-          }
+          mbar_arrive_expect_tx(full + rs, kStageBytes);
+          tma_load_2d(dst, &tmA, 0, ya, full + rs);
+          tma_load_2d(dst + kUPerStage * kABytes, &tmB, 0, yb, full + rs);
+          ya += kUPerStage * 16;
+          yb += kUPerStage * 8;
         }
       }
       // let every copy still in flight land before the CTA's shared memory goes
@@ -338,25 +337,31 @@ __global__ void __maxnreg__(u256::kMaxRegs)
         // 32 KB that held Z_t for those t (consumed by stage-1 batch d, which this quad waited for;
         // the other batches read only their own regions): k-th 2 KB block, rows of 8 pairs 128 B apart
         unsigned char *y = smem + kOffZ + quad * 32768 + (pair >> 3) * 128 + (pair & 7) * 16;
+        // two t and half of the 16 k per pass (8-byte stores of (t, t + 1)): the
+        // real and imaginary columns of both t in flight at once, 48 live values
 #pragma unroll
-        for (int tt = 0; tt < 4; tt += 2) {  // two t per pass: 8-byte stores of (t, t + 1)
-          uint32_t out[16][2];
+        for (int tt = 0; tt < 4; tt += 2) {
 #pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int t = quad * 4 + tt + e;
-            uint32_t r[32];
-            tmem_ld32(tmem + lane_base + t * 32, r);
+          for (int kh = 0; kh < 16; kh += 8) {
+            const int t0 = quad * 4 + tt;
+            uint32_t r[4][8];
+            tmem_ld8(tmem + lane_base + t0 * 32 + kh, r[0]);
+            tmem_ld8(tmem + lane_base + t0 * 32 + 16 + kh, r[1]);
+            tmem_ld8(tmem + lane_base + (t0 + 1) * 32 + kh, r[2]);
+            tmem_ld8(tmem + lane_base + (t0 + 1) * 32 + 16 + kh, r[3]);
             tmem_ld_wait();
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const float2 w = s_tw[t * 16 + k];
-              const float yr = __uint_as_float(r[k]), yi = __uint_as_float(r[16 + k]);
-              out[k][e] = pack_bf2u(fmaf(yr, w.x, -yi * w.y), fmaf(yr, w.y, yi * w.x));
+            for (int k8 = 0; k8 < 8; ++k8) {
+              uint32_t o[2];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const float2 w = s_tw[(t0 + e) * 16 + kh + k8];
+                const float yr = __uint_as_float(r[2 * e][k8]), yi = __uint_as_float(r[2 * e + 1][k8]);
+                o[e] = pack_bf2u(fmaf(yr, w.x, -yi * w.y), fmaf(yr, w.y, yi * w.x));
+              }
+              *reinterpret_cast<uint2 *>(y + (kh + k8) * 2048 + tt * 4) = make_uint2(o[0], o[1]);
             }
           }
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            *reinterpret_cast<uint2 *>(y + k * 2048 + tt * 4) = make_uint2(out[k][0], out[k][1]);
         }
       }
       tc_fence_before();

@@ -619,8 +619,10 @@ int build_tables(mra_handle *h) {
 }
 
 // TMA descriptor of a buffer of k-step tiles seen as a 2-D tensor of 16-bit
-// elements with rows of 256 bytes (128 elements); one load box is one tile
-// of box_rows rows (4 KB particle tiles: 16 rows; 2 KB reference tiles: 8).
+// elements with rows of 256 bytes (128 elements); one load box is box_rows
+// rows, the kUmmaUPerStage consecutive k-step tiles of one pipeline stage
+// (4 KB particle tiles: 16 rows each; 2 KB reference tiles: 8).  Rows past
+// the end read as zero.
 // cuTensorMapEncodeTiled comes from the driver through the runtime's entry
 // point query, so the library needs no link to libcuda.
 int make_tile_map(mra_handle *h, CUtensorMap *tm, void *base, uint64_t rows, uint32_t box_rows, const char *what) {
@@ -679,7 +681,7 @@ int ensure_chunk_workspace(mra_handle *h) {
       if ((rc = dev_alloc(h, &h->A16, h->A16_bytes, "particle k-step tiles"))) return rc;
       cudaError_t e = cudaMemset(h->A16, 0, h->A16_bytes);
       if (e != cudaSuccess) return cuda_err(h, e, "cudaMemset(particle k-step tiles)");
-      if ((rc = make_tile_map(h, &h->tmA, h->A16, static_cast<uint64_t>(utiles) * h->g.NU * 16, 16,
+      if ((rc = make_tile_map(h, &h->tmA, h->A16, static_cast<uint64_t>(utiles) * h->g.NU * 16, 16 * mra::kUmmaUPerStage,
                               "particle k-step tiles")))
         return rc;
       if ((rc = dev_alloc(h, &h->cand, sizeof(int) * mra::kTopRows * chunk, "candidate rows"))) return rc;
@@ -1008,7 +1010,7 @@ int mra_set_refs(mra_t h, const float *d_refs, int32_t K, mra_stream_t stream) {
       if (int rc = dev_alloc(h, &h->B16u, static_cast<size_t>(ktiles) * h->g.NU * 2048, "reference k-step tiles"))
         return rc;
       h->B16u_refs = Kpad;
-      if (int rc = make_tile_map(h, &h->tmB, h->B16u, static_cast<uint64_t>(ktiles) * h->g.NU * 8, 8,
+      if (int rc = make_tile_map(h, &h->tmB, h->B16u, static_cast<uint64_t>(ktiles) * h->g.NU * 8, 8 * mra::kUmmaUPerStage,
                                  "reference k-step tiles"))
         return rc;
     }
@@ -1073,7 +1075,7 @@ int mra_copy_refs(mra_t dst, mra_t src, mra_stream_t stream) {
       if (int rc = dev_alloc(dst, &dst->B16u, static_cast<size_t>(ktiles) * dst->g.NU * 2048, "reference k-step tiles"))
         return rc;
       dst->B16u_refs = Kpad;
-      if (int rc = make_tile_map(dst, &dst->tmB, dst->B16u, static_cast<uint64_t>(ktiles) * dst->g.NU * 8, 8,
+      if (int rc = make_tile_map(dst, &dst->tmB, dst->B16u, static_cast<uint64_t>(ktiles) * dst->g.NU * 8, 8 * mra::kUmmaUPerStage,
                                  "reference k-step tiles"))
         return rc;
     }

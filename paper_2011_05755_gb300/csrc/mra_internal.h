@@ -73,6 +73,7 @@ constexpr int kUmmaRows = 16;   // particle rows per tile
 constexpr int kUmmaRefs = 8;    // references per tile
 constexpr int kUmmaMaxU = 128;  // MMA k-steps per tile
 constexpr int kUmmaMaxG = 64;   // frequency groups
+constexpr int kUmmaUPerStage = 5;  // MMA k-steps per TMA box (one load of each operand per stage)
 
 constexpr int kTc256ChunkKs = 22;
 constexpr int kTc512ChunkKs = 44;

@@ -62,7 +62,12 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t base, uint32_t ncols) {
 }
 
 // Warp-collective TMEM loads (lane i of the warp reads TMEM lane
-// (warp % 4) * 32 + i; columns are 32-bit): 16 or 32 consecutive columns.
+// (warp % 4) * 32 + i; columns are 32-bit): 8, 16 or 32 consecutive columns.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
