@@ -625,21 +625,28 @@ int build_tables(mra_handle *h) {
 // the end read as zero.
 // cuTensorMapEncodeTiled comes from the driver through the runtime's entry
 // point query, so the library needs no link to libcuda.
-int make_tile_map(mra_handle *h, CUtensorMap *tm, void *base, uint64_t rows, uint32_t box_rows, const char *what) {
-  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Encode encode = nullptr;
+using TensorMapEncode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                     const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TensorMapEncode tensor_map_encoder() {
+  static TensorMapEncode encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q{};
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
-      return set_err(h, MRA_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+      return nullptr;
     }
-    encode = reinterpret_cast<Encode>(fn);
+    encode = reinterpret_cast<TensorMapEncode>(fn);
   }
+  return encode;
+}
+
+int make_tile_map(mra_handle *h, CUtensorMap *tm, void *base, uint64_t rows, uint32_t box_rows, const char *what) {
+  const TensorMapEncode encode = tensor_map_encoder();
+  if (!encode) return set_err(h, MRA_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const cuuint64_t dims[2] = {128, rows};
   const cuuint64_t strides[1] = {256};
   const cuuint32_t box[2] = {128, box_rows};
@@ -835,6 +842,25 @@ int run_polar(mra_handle *h, const float *imgs, int64_t n, int rows_per_img, boo
   a.out16 = out16;
   a.fp16 = h->fp16;
   a.umma = h->umma && out16 != nullptr;
+  a.err = h->d_err;
+  a.wait_limit = kWaitLimit;
+  // image staging by a TMA tensor copy: a 3-D map over this call's stack
+  // (rows of L * 4 bytes must be a multiple of 16, the base 16-byte
+  // aligned, the bordered box at most 256 wide); else plain loads
+  {
+    const int L = h->g.L, pad = h->g.taps ? h->g.pad : 0, Lp = L + 2 * pad;
+    const TensorMapEncode encode = (L % 4 == 0 && Lp <= 256 && (reinterpret_cast<uintptr_t>(imgs) & 15) == 0)
+                                       ? tensor_map_encoder() : nullptr;
+    if (encode) {
+      const cuuint64_t dims[3] = {static_cast<cuuint64_t>(L), static_cast<cuuint64_t>(L), static_cast<cuuint64_t>(n)};
+      const cuuint64_t strides[2] = {static_cast<cuuint64_t>(L) * 4, static_cast<cuuint64_t>(L) * L * 4};
+      const cuuint32_t box[3] = {static_cast<cuuint32_t>(Lp), static_cast<cuuint32_t>(Lp), 1};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      a.tma = encode(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(imgs), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+  }
   const int rc = check_launch(h, mra::launch_polar(h->g, a, st), "polar/ring-FFT kernel");
   prof_end(h, rec, 1, st);
   return rc;

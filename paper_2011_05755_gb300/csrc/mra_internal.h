@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only: the library does not link libcuda)
 #include <cuda_runtime.h>
 
 #include "../../include/mra.h"
@@ -92,6 +93,15 @@ struct PolarArgs {
   bool umma;           // out16 in the tcgen05 k-step tile layout
   float *dbg_samples;  // [rows][NS] or null
   float2 *dbg_spec;    // [rows][NBIN] or null
+  // Image staging by one TMA tensor copy per CTA (tma true): a 3-D map over
+  // imgs ({L, L, n_imgs} FP32) whose box is the image in its zero border
+  // ({L + 2 pad, L + 2 pad, 1}, loaded from (-pad, -pad, image); the border
+  // is the map's zero fill) or the bare image (pad 0) of the path's layout.
+  // tma false: plain loads.
+  CUtensorMap tmap;
+  bool tma;
+  int *err;              // device flag: bit 0 = the staging wait timed out
+  uint32_t wait_limit;   // polls before that wait gives up
 };
 
 struct CCArgs {

@@ -24,6 +24,7 @@
 #include "dev_util.cuh"
 #include "mra_internal.h"
 #include "ring_fft.cuh"
+#include "tma.cuh"
 
 namespace mra {
 
@@ -117,14 +118,15 @@ __host__ __device__ inline int image_floats(const Geometry &g, bool taps) {
 }
 
 template <int R, bool TAPS, int OUT>
-__global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs a) {
+__global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, const __grid_constant__ PolarArgs a) {
   extern __shared__ float4 smem_f4[];
   const int L = g.L, NS = g.NS, M = g.M;
   const int NSp = sample_stride(NS);
   const int LL = L * L;
   const int64_t img = blockIdx.y;
   float *im = reinterpret_cast<float *>(smem_f4);       // the image (with its zero border if TAPS)
-  float2 *tws = reinterpret_cast<float2 *>(im + image_floats(g, TAPS));  // [M] forward twiddles
+  uint64_t *ibar = reinterpret_cast<uint64_t *>(im + image_floats(g, TAPS));  // image copy barrier (16 B)
+  float2 *tws = reinterpret_cast<float2 *>(im + image_floats(g, TAPS) + 4);  // [M] forward twiddles
   int *s_kpos = reinterpret_cast<int *>(tws + M);       // [M/2 + 1] output bases (padded to even)
   float *smem = reinterpret_cast<float *>(s_kpos + ((M / 2 + 2) & ~1));  // [R][NSp] samples, then ring FFTs
   const float c0 = 0.5f * static_cast<float>(L);
@@ -140,7 +142,20 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs
   }
   const float *src = a.imgs + img * LL;
   const bool vec = (L & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
-  if constexpr (TAPS) {
+  // TMA staging: one tensor copy of the image (and, with TAPS, its zero
+  // border from the map's out-of-bounds fill), issued by thread 0 while the
+  // CTA loads its tables; the destination must be 128-byte aligned
+  const bool tma = a.tma && (smem_u32(im) & 127u) == 0;
+  if (tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(ibar, 1);
+      mbar_init_fence();
+      const int pad = TAPS ? g.pad : 0;
+      const int Lp = L + 2 * pad;
+      mbar_arrive_expect_tx(ibar, static_cast<uint32_t>(Lp * Lp) * 4u);
+      tma_load_3d(im, &a.tmap, -pad, -pad, static_cast<int>(img), ibar);
+    }
+  } else if constexpr (TAPS) {
     // zero the bordered buffer, then copy the interior (pad is a multiple of 4)
     const int Lp = L + 2 * g.pad;
     for (int i = threadIdx.x; i < image_floats(g, true) / 4; i += blockDim.x)
@@ -168,6 +183,17 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, PolarArgs
     }
   }
   for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = g.fwd_tw[i];
+  if (tma) {
+    __syncthreads();  // the barrier's initialisation is visible to every thread
+    const bool ok = mbar_wait_bounded(ibar, 0, a.wait_limit);
+    if (__syncthreads_or(!ok)) {  // uniform: every thread leaves
+      if (threadIdx.x == 0) {
+        atomicOr(a.err, 1);
+        mbar_wait_bounded(ibar, 0, a.wait_limit);  // the copy must land before the CTA's memory goes
+      }
+      return;
+    }
+  }
   __syncthreads();
 
   for (int s0 = blockIdx.x * R; s0 < a.rows_per_img; s0 += gridDim.x * R) {
@@ -352,10 +378,11 @@ static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t 
   return cudaGetLastError();
 }
 
-// Shared memory of a CTA with R rows: the staged image, the twiddles, the
-// output bases, then per row the samples and (16-bit output) the planes.
+// Shared memory of a CTA with R rows: the staged image, its copy barrier,
+// the twiddles, the output bases, then per row the samples and (16-bit
+// output) the planes.
 inline size_t polar_smem_bytes(const Geometry &g, bool taps, bool out16, int R) {
-  const size_t fixed = static_cast<size_t>(image_floats(g, taps)) * sizeof(float) + g.M * sizeof(float2) +
+  const size_t fixed = static_cast<size_t>(image_floats(g, taps)) * sizeof(float) + 16 + g.M * sizeof(float2) +
                        static_cast<size_t>((g.M / 2 + 2) & ~1) * sizeof(int);
   size_t per_row = static_cast<size_t>(sample_stride(g.NS)) * sizeof(float);
   if (out16) per_row += static_cast<size_t>(g.KS) * 16 * sizeof(uint32_t);

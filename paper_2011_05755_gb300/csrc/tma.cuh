@@ -1,5 +1,5 @@
-// Bulk asynchronous copies global -> shared (TMA, cp.async.bulk) completed
-// through an mbarrier, with a bounded wait.
+// Bulk asynchronous copies global -> shared (TMA: cp.async.bulk and the
+// tensor-map form) completed through an mbarrier, with a bounded wait.
 #pragma once
 
 #include <cstdint>
@@ -39,6 +39,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One box of a 3-D tensor map (x innermost) into shared memory, completing
+// on `bar`.  x * element size must be a multiple of 16 bytes; coordinates
+// outside the tensor read the map's fill value (zero).
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
 }
 
