@@ -53,6 +53,8 @@ def parse():
                          "extra measurements, e.g. mra_n50k_L128_K200_shift6)")
     ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests in each serving run (Poisson streams at 0.5, 0.7 and 0.9 x capacity); 0 skips it")
+    ap.add_argument("--kernel", default="tuned", choices=["tuned", "mma_sync", "tcgen05"],
+                    help="contraction kernel of the 16-bit M = 256 path: the autotuner's choice (default) or a fixed one")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the larger-box workload leg (128 px, K = 200, 169 shifts, three precisions)")
     return ap.parse_args()
@@ -290,7 +292,12 @@ def main():
         rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
         # launch choices of this configuration from the autotuner (timed candidates, cached in JSON)
         from paper_2011_05755_gb300.autotune import tune
-        choice = tune(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, prec_code, K)
+        if args.kernel == "tuned" or prec_code == mra.MRA_FP32:
+            choice = tune(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, prec_code,
+                          K)
+        else:  # a fixed kernel (profiling runs): the library's default chunking
+            choice = {"kernel": {"mma_sync": mra.MRA_KERNEL_MMA_SYNC, "tcgen05": mra.MRA_KERNEL_TCGEN05}[args.kernel],
+                      "chunk_images": 0, "candidates": []}
         al = mra.Aligner(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror,
                          prec_code, choice["chunk_images"], choice["kernel"])
         poses = torch.empty((n, 8), dtype=torch.int32, device=dev)
