@@ -130,8 +130,8 @@ typedef struct {
  * launches would need more than 227 KB of shared memory per CTA (the
  * message names it; e.g. on the 16-bit paths the polar kernel's CTA holds
  * the image in a zero border, one row's ring samples and its 16-bit
- * spectrum words, which exceeds the limit beyond about L = 136 with rings
- * up to 65 or L = 100 with rings up to 81); MRA_ECUDA if a CUDA call
+ * spectrum words, which exceeds the limit from L = 146 with rings up to
+ * 65, or from L = 100 with rings up to 81); MRA_ECUDA if a CUDA call
  * fails. */
 int mra_create(const mra_config_t *cfg, mra_t *out);
 
@@ -224,10 +224,12 @@ int mra_run_host(mra_t h, const float *h_refs, int32_t K, const float *h_imgs, i
  * launch on `stream`.  The first call with a given set of buffers and sizes
  * runs the three calls one after the other (sizing and allocating every
  * workspace); the second captures them into a graph (on a stream of the
- * handle; nothing runs during the capture) and launches it, and every later
- * call with the same buffers and sizes replays it.  A call with other buffers or sizes drops
- * the graph and starts again.  The buffers' contents may change between
- * calls; their addresses and sizes must not while a graph is cached.
+ * handle; nothing runs during the capture) and launches it, and every
+ * later call with the same buffers and sizes replays it.  A call with
+ * other buffers or sizes drops the graph and starts again.  The buffers'
+ * contents may change between calls; their addresses and sizes must not
+ * while a graph is cached (the graph holds them, and the TMA descriptor of
+ * the image stack).
  * Stage timing (mra_profile) records only the eager calls.  Same errors as
  * the three calls; MRA_ECUDA if capture or instantiation fails.  No
  * counterpart in the paper: this is launch plumbing. */

@@ -70,3 +70,10 @@ def test_traffic_is_close_to_the_algorithmic_bytes():
     assert 0.97 * tc256 <= table["cc_tc256_kernel"]["bytes_per_unit"] <= 1.2 * tc256
     assert 0.97 * tc512 <= table["cc_tc512_kernel"]["bytes_per_unit"] <= 1.2 * tc512
     assert 0.95 * polar <= table["polar_fft_kernel"]["bytes_per_unit"] <= 1.2 * polar
+    # tcgen05 path: frequencies four to an MMA in f order, a group's k-steps those of its lowest
+    # frequency; 4 KB of particle operand per 16 rows and k-step
+    rings = bench.ring_table(1, 35, 1)
+    nu = sum(-(-sum(1 for _, n in rings if n // 2 >= f) // 16) for f in range(0, 129, 4))
+    assert nu == 55
+    umma = nu * 4096 / 16 / 100 + 8
+    assert 0.97 * umma <= table["cc_umma256_kernel"]["bytes_per_unit"] <= 1.2 * umma
