@@ -47,11 +47,11 @@ __host__ __device__ constexpr bool out_is_umma(int out) { return out == kOutUBF1
 template <int OUT>
 __device__ __forceinline__ uint32_t pack_qp(float q, float p) {
   if constexpr (out_is_fp16(OUT)) {
-    return static_cast<uint32_t>(__half_as_ushort(__float2half_rn(q))) |
-           (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(p))) << 16);
+    const __half2 h = __floats2half2_rn(q, p);  // .x (low half) = q
+    return *reinterpret_cast<const uint32_t *>(&h);
   } else {
-    return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(q))) |
-           (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(p))) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(q, p);
+    return *reinterpret_cast<const uint32_t *>(&h);
   }
 }
 
@@ -61,6 +61,25 @@ __device__ __forceinline__ uint32_t pack_qp(float q, float p) {
 // apart, same word) fall in different banks.  The XOR keeps word pairs
 // (2j, 2j + 1) adjacent.
 __device__ __forceinline__ int plane_swz(int w) { return w ^ ((w >> 4) & 14); }
+
+// One bin of a particle or reference row into the path's output layout
+// (weights for references, the debug copy, FP32 tiles or 16-bit words).
+template <int OUT>
+__device__ __forceinline__ void put_bin(const Geometry &g, const PolarArgs &a, uint32_t *planes_row, const int *s_kpos,
+                                        int ring, int bin0, int64_t row, int k, float2 X) {
+  if (a.weighted) {
+    const float w = g.bweight[bin0 + k];
+    X.x *= w;
+    X.y *= w;
+  }
+  if (a.dbg_spec) a.dbg_spec[row * g.NBIN + bin0 + k] = X;
+  if constexpr (OUT == kOutF32) {
+    if (a.out) a.out[((row >> 3) * g.NB + s_kpos[k] + ring) * kTile + (row & 7)] = X;
+  } else {
+    const int w = s_kpos[k] + ring;  // k-step w / 16, word w % 16 of it
+    planes_row[plane_swz(w)] = pack_qp<OUT>(X.x - X.y, X.x + X.y);
+  }
+}
 
 // All (ring, row) jobs of one ring-length class [i0, i1) of a CTA: forward
 // FFT of the packed samples, real split, weights, and the spectrum written in
@@ -81,28 +100,22 @@ __device__ __forceinline__ int ring_class(const Geometry &g, const PolarArgs &a,
     const int job = j0 + lane / T;
     const bool active = job < njobs;
     const int jc = active ? job : j0;
-    const int ring = i0 + jc / nrows;
-    const int i = jc % nrows;
+    // (ring, row) of the job; nrows is R except in an image's last group
+    const int ring = i0 + (nrows == R ? jc / R : jc / nrows);
+    const int i = nrows == R ? jc % R : jc % nrows;
     const int4 rd = g.rings[ring];  // {N, sample offset, natural-bin offset, log2(N/2)}
     float2 *z = reinterpret_cast<float2 *>(smem + i * sample_stride(g.NS) + rd.y);
     group_fft<H>(z, t, active, tws, g.M);
     if (active) {
       const int wstep = g.M / (2 * H);
       const int64_t row = row0 + i;
-      for (int k = t; k <= H; k += T) {
-        float2 X = real_split(z, H, k, tws[k * wstep]);
-        if (a.weighted) {
-          const float w = g.bweight[rd.z + k];
-          X.x *= w;
-          X.y *= w;
-        }
-        if (a.dbg_spec) a.dbg_spec[row * g.NBIN + rd.z + k] = X;
-        if constexpr (OUT == kOutF32) {
-          if (a.out) a.out[((row >> 3) * g.NB + s_kpos[k] + ring) * kTile + (row & 7)] = X;
-        } else {
-          const int w = s_kpos[k] + ring;  // k-step w / 16, word w % 16 of it
-          planes[i * NB16 + plane_swz(w)] = pack_qp<OUT>(X.x - X.y, X.x + X.y);
-        }
+      uint32_t *prow = planes + i * NB16;
+      // bins k and H - k from one pair of loads and one twiddle
+      for (int k = t; 2 * k <= H; k += T) {
+        float2 xk, xhk;
+        real_split_pair(z, H, k, tws[k * wstep], xk, xhk);
+        put_bin<OUT>(g, a, prow, s_kpos, ring, rd.z, row, k, xk);
+        if (2 * k != H) put_bin<OUT>(g, a, prow, s_kpos, ring, rd.z, row, H - k, xhk);
       }
     }
     __syncwarp();
@@ -299,7 +312,7 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, const __g
       // of MMA k-step tile u = umap[kk] / 4 (slot = umap[kk] % 4)
       unsigned char *out = reinterpret_cast<unsigned char *>(a.out16);
       for (int idx = threadIdx.x; idx < g.KS * 2 * nrows; idx += blockDim.x) {
-        const int i = idx % nrows, rem = idx / nrows;
+        const int i = nrows == R ? idx % R : idx % nrows, rem = nrows == R ? idx / R : idx / nrows;
         const int hh = rem & 1, kk = rem >> 1;
         const int64_t row = row0 + i;
         const int um = __ldg(g.umap + kk);
@@ -322,7 +335,7 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, const __g
       __syncthreads();
       const int per_k = nrows * 4;
       for (int idx = threadIdx.x; idx < g.KS * per_k; idx += blockDim.x) {
-        const int kk = idx / per_k;
+        const int kk = nrows == R ? idx / (4 * R) : idx / per_k;
         const int rem = idx - kk * per_k;
         const int i = rem >> 2, t = rem & 3;
         const int64_t row = row0 + i;

@@ -149,4 +149,19 @@ __device__ __forceinline__ float2 real_split(const float2 *z, int H, int k, floa
   return cadd(e, cmul(w, o));
 }
 
+// Bins k and H - k (0 <= k <= H / 2) of the same real DFT from one pair of
+// spectrum loads and one twiddle: with E, O as in real_split,
+// X(k) = E + w^k O and X(H - k) = conj(E - w^k O), since the odd part of
+// bin H - k is conj(O) and w^(H - k) = -conj(w^k).  For k = H / 2 both
+// entries are the same bin.
+__device__ __forceinline__ void real_split_pair(const float2 *z, int H, int k, float2 w, float2 &xk, float2 &xhk) {
+  const float2 zk = z[k & (H - 1)];
+  const float2 zc = cconj(z[(H - k) & (H - 1)]);
+  const float2 e = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+  const float2 d = csub(zk, zc);
+  const float2 wo = cmul(w, make_float2(0.5f * d.y, -0.5f * d.x));
+  xk = cadd(e, wo);
+  xhk = cconj(csub(e, wo));
+}
+
 }  // namespace mra
