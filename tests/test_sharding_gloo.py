@@ -101,7 +101,8 @@ def _gpu_worker(rank, world, port, imgs, refs, poses, cfg, K, out):
     comp = torch.zeros_like(sums)
     counts = torch.zeros((K,), dtype=torch.int32, device="cuda")
     if b > a:
-        mra.mra_class_sums(al.h, imgs[a:b].cuda().contiguous(), poses[a:b].cuda().contiguous(), sums, comp, counts)
+        mra.mra_class_sums(al.h, imgs[a:b].cuda().contiguous(), torch.from_numpy(poses[a:b]).cuda().contiguous(),
+                           sums, comp, counts)
     hs, hc, hn = sums.cpu(), comp.cpu(), counts.cpu()
     allreduce_class_sums(hs, hc, hn)
     avg = torch.zeros((K, L, L), device="cuda")
@@ -154,5 +155,7 @@ def _unsharded_worker(imgs, refs, cfg, out):
     al.set_refs(refs.cuda())
     poses = al.align(imgs.cuda())
     avg, cnt = al.average(imgs.cuda(), poses)
-    out.put((poses.cpu(), avg.cpu().numpy(), cnt.cpu().numpy()))
+    # NumPy arrays travel by value: a tensor would travel as a file descriptor that can vanish when
+    # this process exits before the parent has received it
+    out.put((poses.cpu().numpy(), avg.cpu().numpy(), cnt.cpu().numpy()))
     al.close()
