@@ -52,6 +52,9 @@ CASES = {
     "M256_nomirror": (64, 2, 30, 1, 2.0, 1.0, 0, 9, 3),
     # rings beyond 64 at L = 132 (the 16-bit paths' FP32 rescore keeps each ring's spectrum in its samples)
     "M512_r65": (132, 1, 65, 1, 1.0, 1.0, 1, 3, 2),
+    # a box whose rows are not a multiple of 16 bytes: the polar kernel stages the image with plain loads
+    # instead of the TMA tensor copy
+    "M128_L30": (30, 1, 12, 1, 2.0, 1.0, 1, 5, 3),
 }
 
 
