@@ -5,7 +5,7 @@ shifts) take seconds of oracle time per image, so the tables are computed
 by worker processes started with ``spawn`` (a pool forked after the CUDA
 context exists would hang).  Each worker returns, per image, the oracle's
 pose (argmax with the tie rule), its runner-up gap and the ``top`` largest
-entries of the table with their indices, enough to judge a GPU pose that
+entries of the table with their indices, enough to assess a GPU pose that
 differs from the oracle's in a near tie without shipping whole tables.
 """
 from __future__ import annotations
