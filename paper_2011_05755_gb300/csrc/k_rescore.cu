@@ -10,6 +10,8 @@
 
 namespace mra {
 
+constexpr int kRescoreThreads = 256;  // 8 warps per CTA (one image)
+
 // ---------------------------------------------------------------------------
 // FP32 rescore: for each candidate row of an image, resample at its shift,
 // ring-FFT, contract with its reference in FP32, inverse DFT; keep the best
@@ -17,7 +19,7 @@ namespace mra {
 // One CTA per image.
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a) {
+__global__ void __launch_bounds__(kRescoreThreads) rescore_kernel(Geometry g, RescoreArgs a) {
   constexpr int T = IfftShape<M>::T;
   constexpr int U = IfftShape<M>::U;
   extern __shared__ float4 smem_f4[];
@@ -45,6 +47,12 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
   }
   for (int i = threadIdx.x; i < NR; i += blockDim.x) s_rings[i] = g.rings[i];
   unsigned long long best = 0ull;
+  __syncthreads();
+  // Warp 0 runs each candidate's inverse DFT at the end of its iteration;
+  // warps 1-7 resample the next candidate meanwhile (its samples are not
+  // read by the inverse DFT, and warp 0 joins the barrier after resampling
+  // only once its inverse DFT is done, before the spectrum buffer is
+  // rewritten).
   for (int c = 0; c < kTopRows; ++c) {
     const int rowid = a.cand[img * kTopRows + c];
     if (rowid < 0) continue;  // uniform over the CTA
@@ -52,14 +60,15 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
     const int rs = rowid >> 1;
     const int s = rs % S;
     const int k = rs / S;
-    __syncthreads();
-    const float2 sh = g.shifts[s];
-    for (int q = threadIdx.x; q < NS; q += blockDim.x) {
-      const float2 o = g.offs[q];
-      samp[q] = bilinear_smem(im, L, c0 + sh.x + o.x, c0 + sh.y + o.y);
+    if (warp > 0) {
+      const float2 sh = g.shifts[s];
+      for (int q = threadIdx.x - 32; q < NS; q += blockDim.x - 32) {
+        const float2 o = g.offs[q];
+        samp[q] = bilinear_smem(im, L, c0 + sh.x + o.x, c0 + sh.y + o.y);
+      }
     }
     __syncthreads();
-    for (int ring = NR - 1 - warp; ring >= 0; ring -= 8) {
+    for (int ring = NR - 1 - warp; ring >= 0; ring -= kRescoreThreads / 32) {
       const int4 rd = s_rings[ring];
       const int N = rd.x, H = N >> 1;
       float2 *z = reinterpret_cast<float2 *>(samp + rd.y);
@@ -81,14 +90,23 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
       __syncwarp();
     }
     __syncthreads();
-    // FP32 contraction with reference k for every frequency: two threads per
-    // frequency (alternate rings, partial sums combined by a shuffle), the
-    // reference loads of four rings in flight at a time
+    // FP32 contraction with reference k for every frequency: the lowest n2
+    // frequencies (the most rings) by two threads each (alternate rings,
+    // partial sums combined by a shuffle), the others by one thread, n2 as
+    // large as fills the fewest whole passes of the CTA (M = 256: 129
+    // frequencies in one pass; M = 512: 257 in two); the reference loads of
+    // four rings in flight at a time
+    constexpr int NF = M / 2 + 1;
+    constexpr int kPasses = (NF + kRescoreThreads - 1) / kRescoreThreads;
+    constexpr int n2 = NF < kPasses * kRescoreThreads - NF ? NF : kPasses * kRescoreThreads - NF;
+    constexpr int NITEMS = NF + n2;
     const float2 *Bk = a.B + static_cast<int64_t>(k / kTile) * g.NB * kTile + (k % kTile);
-    for (int it0 = 0; it0 < 2 * (M / 2 + 1); it0 += blockDim.x) {  // uniform trip count (shuffles below)
+    for (int it0 = 0; it0 < NITEMS; it0 += blockDim.x) {  // uniform trip count (shuffles below)
       const int it = it0 + threadIdx.x;
-      const bool active = it < 2 * (M / 2 + 1);
-      const int f = active ? it >> 1 : 0, half = it & 1;
+      const bool active = it < NITEMS;
+      const bool split = it < 2 * n2;  // even count: the one-thread items start on an even lane
+      const int f = !active ? 0 : (split ? it >> 1 : n2 + (it - 2 * n2));
+      const int half = split ? (it & 1) : 0, step = split ? 2 : 1;
       float p1 = 0.f, p2 = 0.f, p3 = 0.f, p4 = 0.f;
       if (active) {
         // rings with N_r / 2 >= f are a suffix [lo, NR) of the (ascending) ring list
@@ -100,7 +118,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
         }
         const float2 *Bf = Bk + static_cast<int64_t>(g.kpos[f]) * kTile;  // bin (ring, f) at kpos[f] + ring
 #pragma unroll 4
-        for (int ring = NR - 1 - half; ring >= lo; ring -= 2) {
+        for (int ring = NR - 1 - half; ring >= lo; ring -= step) {
           const int4 rd = s_rings[ring];
           const float2 *zr = reinterpret_cast<const float2 *>(samp + rd.y);
           const float2 z0 = zr[0];
@@ -112,11 +130,15 @@ __global__ void __launch_bounds__(256) rescore_kernel(Geometry g, RescoreArgs a)
           p4 = fmaf(A.y, Bv.x, p4);
         }
       }
-      // items 2f and 2f + 1 are neighbouring lanes of one warp
-      p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-      p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
-      p3 += __shfl_xor_sync(0xffffffffu, p3, 1);
-      p4 += __shfl_xor_sync(0xffffffffu, p4, 1);
+      // the two items of a split frequency are neighbouring lanes of one warp
+      const float q1 = __shfl_xor_sync(0xffffffffu, p1, 1), q2 = __shfl_xor_sync(0xffffffffu, p2, 1);
+      const float q3 = __shfl_xor_sync(0xffffffffu, p3, 1), q4 = __shfl_xor_sync(0xffffffffu, p4, 1);
+      if (split) {
+        p1 += q1;
+        p2 += q2;
+        p3 += q3;
+        p4 += q4;
+      }
       if (active && half == 0) {
         Z[f] = make_float2((p1 + p2) - (p3 + p4), (p3 - p4) + (p1 - p2));
         if (f != 0 && f != M / 2) Z[M - f] = make_float2((p1 + p2) + (p3 + p4), (p1 - p2) - (p3 - p4));
@@ -171,7 +193,7 @@ static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cud
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
-  rescore_kernel<M><<<static_cast<unsigned>(a.n), 256, smem, st>>>(g, a);
+  rescore_kernel<M><<<static_cast<unsigned>(a.n), kRescoreThreads, smem, st>>>(g, a);
   return cudaGetLastError();
 }
 
