@@ -259,6 +259,20 @@ __device__ __forceinline__ float warp_max2(float u, float m, int lane) {
   return v;
 }
 
+// Maxima over the 32 lanes of four values per lane, the (u, m) maxima of
+// two pairs A and B, in 6 shuffles: afterwards lanes 0-7 hold max(uA), 8-15
+// max(mA), 16-23 max(uB) and 24-31 max(mB).
+__device__ __forceinline__ float warp_max4(float uA, float mA, float uB, float mB, int lane) {
+  const bool hb = (lane & 16) != 0;  // this half keeps pair B and sends pair A
+  float x = fmaxf(hb ? uB : uA, __shfl_xor_sync(0xffffffffu, hb ? uA : uB, 16));
+  float y = fmaxf(hb ? mB : mA, __shfl_xor_sync(0xffffffffu, hb ? mA : mB, 16));
+  const bool hm = (lane & 8) != 0;   // this quarter keeps m and sends u
+  float v = fmaxf(hm ? y : x, __shfl_xor_sync(0xffffffffu, hm ? x : y, 8));
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // M = 256 kernel: one CTA per tile of 8 rows, looping over the reference
 // tiles of 8 (64 pairs each), 8 warps, two CTAs per SM.  Phase 1 streams a
 // tile's A and B fragments in chunks of whole frequencies (at most
@@ -407,17 +421,33 @@ __global__ void __launch_bounds__(kTc256Threads, 2) cc_tc256_kernel(Geometry g, 
     // ---------------- Phase 2: tensor-core inverse DFT, row maxima ----------------
     const int ref = kt * 8 + warp;  // pairs warp + 8 i: reference `warp` of the tile, row i
     const int nvalid = ref < a.K ? static_cast<int>(min(static_cast<int64_t>(8), a.rows - rt * 8)) : 0;
+    // the row maxima of two consecutive pairs are reduced over the warp together
+    float su = -INFINITY, sm = -INFINITY;  // the even pair's lane maxima
+    int64_t sbase = 0;
 #pragma unroll 1
     for (int i = 0; i < nvalid; ++i) {  // padding pairs are skipped (warp-uniform)
       const int pc = 8 * i + warp;
       const int2 ri = rinfo[i];
-      float *dbg = a.dbg_cc ? a.dbg_cc + ((static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y) * 2 * M : nullptr;
+      const int64_t rbase = (static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y;
+      float *dbg = a.dbg_cc ? a.dbg_cc + rbase * 2 * M : nullptr;
       float vu, vm;
       pair_idft_tc256(Zw + pc * M, z256_swz(pc), Ln, a1, b2, lane, vu, vm, dbg);
-      const float best = warp_max2(vu, vm, lane);
-      if ((lane & 15) == 0)
-        a.rowmax[((static_cast<int64_t>(ri.x) * a.K + ref) * S + ri.y) * 2 + (lane >> 4)] =
-            (lane && !g.mirror) ? -INFINITY : best;
+      if ((i & 1) == 0 && i + 1 < nvalid) {
+        su = vu;
+        sm = vm;
+        sbase = rbase;
+        continue;
+      }
+      if (i & 1) {
+        const float v = warp_max4(su, sm, vu, vm, lane);
+        if ((lane & 7) == 0) {
+          const bool mrow = (lane & 8) != 0;
+          a.rowmax[((lane & 16) ? rbase : sbase) * 2 + mrow] = (mrow && !g.mirror) ? -INFINITY : v;
+        }
+      } else {  // the last pair of an odd count
+        const float best = warp_max2(vu, vm, lane);
+        if ((lane & 15) == 0) a.rowmax[rbase * 2 + (lane >> 4)] = (lane && !g.mirror) ? -INFINITY : best;
+      }
     }
     __syncthreads();  // the next tile's contraction overwrites the pair buffers
   }
@@ -637,6 +667,7 @@ __global__ void __launch_bounds__(kTc512Threads, 1) cc_tc512_kernel(Geometry g, 
             dbg[M + n] = c2i;        // Im c(n + 256) at n
           }
         }
+      // (reducing two pairs together as the M = 256 kernel does needs registers this kernel does not have)
       const float best = warp_max2(vu, vm, lane);
       if ((lane & 15) == 0) a.rowmax[rbase * 2 + (lane >> 4)] = (lane && !g.mirror) ? -INFINITY : best;
     }
