@@ -197,6 +197,31 @@ static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cud
   return cudaGetLastError();
 }
 
+template <int M>
+static int rescore_occupancy_t(const Geometry &g) {
+  const size_t smem = rescore_smem(g);
+  int n = 0;
+  if (cudaFuncSetAttribute(rescore_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rescore_kernel<M>, kRescoreThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int rescore_ctas_per_sm(const Geometry &g) {
+  switch (g.M) {
+    case 16: return rescore_occupancy_t<16>(g);
+    case 32: return rescore_occupancy_t<32>(g);
+    case 64: return rescore_occupancy_t<64>(g);
+    case 128: return rescore_occupancy_t<128>(g);
+    case 256: return rescore_occupancy_t<256>(g);
+    case 512: return rescore_occupancy_t<512>(g);
+    default: return 0;
+  }
+}
+
 cudaError_t launch_rescore(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   switch (g.M) {

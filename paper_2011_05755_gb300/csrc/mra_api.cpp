@@ -677,6 +677,23 @@ int ensure_chunk_workspace(mra_handle *h) {
     if (chunk > 65535) chunk = 65535;
     const int64_t max_chunk = (int64_t(65535) * mra::kTile) / S;
     if (chunk > max_chunk) chunk = static_cast<int>(max_chunk < 1 ? 1 : max_chunk);
+    if (h->cfg.chunk_images <= 0 && h->half) {
+      // the default chunk in whole waves of the FP32 rescore (one CTA per
+      // image) when that costs at most a tenth of it: a chunk that ends with
+      // a nearly empty wave leaves most SMs idle for one rescore CTA's time
+      // (the polar kernel's waves, four CTAs per image at two per SM, divide
+      // the same count at L = 76)
+      int dev = 0, sms = 0;
+      const int occ = mra::rescore_ctas_per_sm(h->g);
+      if (occ > 0 && cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+        const int wave = occ * sms;
+        const int whole = chunk / wave * wave;
+        if (whole > 0 && 10 * static_cast<int64_t>(whole) >= 9 * static_cast<int64_t>(chunk)) chunk = whole;
+      } else {
+        cudaGetLastError();
+      }
+    }
     h->chunk = chunk;
     const int64_t tiles = (int64_t(chunk) * S + mra::kTile - 1) / mra::kTile;
     int rc;

@@ -152,6 +152,7 @@ cudaError_t launch_cc_tc(const Geometry &g, const TcArgs &a, bool fp16, cudaStre
 cudaError_t launch_top8(const float *rowmax, int64_t n, int nrows, int *cand, cudaStream_t st);
 cudaError_t launch_rescore(const Geometry &g, const RescoreArgs &a, cudaStream_t st);
 size_t rescore_smem(const Geometry &g);
+int rescore_ctas_per_sm(const Geometry &g);  // resident rescore CTAs per SM (0 if unknown)
 // Shared memory of one CTA of the polar kernel with one row, of the FP32
 // contraction kernel, and the per-CTA opt-in limit of the device.
 size_t polar_smem_one_row(const Geometry &g, bool taps, bool out16);
