@@ -183,9 +183,10 @@ size_t rescore_smem(const Geometry &g) {
          static_cast<size_t>(g.NS) * sizeof(float) + 16 + static_cast<size_t>(g.NR) * sizeof(int4);
 }
 
+// The kernel's dynamic shared-memory limit only ever grows (handles of
+// several geometries share the kernel).
 template <int M>
-static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
-  const size_t smem = rescore_smem(g);
+static cudaError_t rescore_smem_attr(size_t smem) {
   static size_t attr_set = 0;
   if (attr_set < smem) {
     cudaError_t e =
@@ -193,6 +194,14 @@ static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cud
     if (e != cudaSuccess) return e;
     attr_set = smem;
   }
+  return cudaSuccess;
+}
+
+template <int M>
+static cudaError_t launch_rescore_t(const Geometry &g, const RescoreArgs &a, cudaStream_t st) {
+  const size_t smem = rescore_smem(g);
+  cudaError_t e = rescore_smem_attr<M>(smem);
+  if (e != cudaSuccess) return e;
   rescore_kernel<M><<<static_cast<unsigned>(a.n), kRescoreThreads, smem, st>>>(g, a);
   return cudaGetLastError();
 }
@@ -201,8 +210,7 @@ template <int M>
 static int rescore_occupancy_t(const Geometry &g) {
   const size_t smem = rescore_smem(g);
   int n = 0;
-  if (cudaFuncSetAttribute(rescore_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-          cudaSuccess ||
+  if (rescore_smem_attr<M>(smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rescore_kernel<M>, kRescoreThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;

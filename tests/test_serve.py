@@ -193,6 +193,7 @@ def test_results_same_alone_and_in_the_mix(mra, prec):
         alone = fresh()[r.rid]
         alone.imgs = r.imgs
         Server(Scheduler(2**30, 1, 1), exe).run([alone])
+        assert not alone.error, (r.rid, alone.error)
         assert torch.equal(alone.poses, r.poses), r.rid
         r1, r2 = serving_rings(r.L)
         a = mra.Aligner(r.L, r1, r2, 1, 3.0, 1.0, 1, precision)
