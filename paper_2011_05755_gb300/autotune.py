@@ -7,8 +7,10 @@ The library exposes two launch choices per handle (``mra_config_t``):
   kernel (tiles of 16 rows x 8 references, TMEM accumulators, one persistent
   CTA per SM);
 * ``chunk_images``: images per internal chunk (the particle spectra of one
-  chunk are the largest workspace; fewer, larger chunks mean fewer launches,
-  smaller ones a smaller footprint).
+  chunk are the largest workspace; fewer, larger chunks mean fewer launches
+  and kernel tails, smaller ones a smaller footprint).  Candidates: the
+  library's default (a 2 GiB workspace, rounded to whole rescore waves),
+  1,024 images, and three times the default.
 
 :func:`tune` times every candidate on a synthetic stack of the
 configuration's shape (the alignment's work does not depend on the pixel
@@ -90,7 +92,9 @@ def tune(L: int, first_ring: int, last_ring: int, ring_step: int = 1, shift_rang
     poses = torch.empty((n_probe, 8), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     results = []
-    for kernel, chunk in candidates(first_ring, last_ring, ring_step, precision):
+    todo = list(candidates(first_ring, last_ring, ring_step, precision))
+    while todo:
+        kernel, chunk = todo.pop(0)
         al = Aligner(L, first_ring, last_ring, ring_step, shift_range, shift_step, mirror, precision, chunk, kernel)
         try:
             al.set_refs(refs, stream)
@@ -104,8 +108,11 @@ def tune(L: int, first_ring: int, last_ring: int, ring_step: int = 1, shift_rang
             e1.record(stream)
             mra_sync(al.h, stream)
             ms = e0.elapsed_time(e1) / reps
+            used = al.info["chunk_images"]
             results.append({"kernel": kernel, "chunk_images": chunk, "ms_per_image": ms / n_probe,
-                            "chunk_used": al.info["chunk_images"]})
+                            "chunk_used": used})
+            if chunk == 0 and 3 * used < n_probe:  # three default chunks in one (whole waves stay whole)
+                todo.append((kernel, 3 * used))
         finally:
             al.close()
     best = min(results, key=lambda r: r["ms_per_image"])
