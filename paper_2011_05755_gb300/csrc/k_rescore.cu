@@ -18,8 +18,12 @@ constexpr int kRescoreThreads = 256;  // 8 warps per CTA (one image)
 // (value, smallest index) over the candidates' angles as the argmax key.
 // One CTA per image.
 // ---------------------------------------------------------------------------
+// Registers are held to 64 per thread for M = 32..256, so that four CTAs
+// (images) fit on an SM where their shared memory allows (the 76-pixel
+// workload).
 template <int M>
-__global__ void __launch_bounds__(kRescoreThreads) rescore_kernel(Geometry g, RescoreArgs a) {
+__global__ void __launch_bounds__(kRescoreThreads, (M >= 32 && M <= 256) ? 4 : 1)
+    rescore_kernel(Geometry g, RescoreArgs a) {
   constexpr int T = IfftShape<M>::T;
   constexpr int U = IfftShape<M>::U;
   extern __shared__ float4 smem_f4[];
@@ -40,7 +44,29 @@ __global__ void __launch_bounds__(kRescoreThreads) rescore_kernel(Geometry g, Re
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int NR = g.NR;
 
-  for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(a.imgs + img * LL + i);
+  {
+    // the image, four 16-byte loads in flight per thread (when the rows allow)
+    const float *src = a.imgs + img * LL;
+    if ((LL & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+      float4 *d4 = reinterpret_cast<float4 *>(im);
+      for (int i0 = threadIdx.x; i0 < LL / 4; i0 += 4 * blockDim.x) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * blockDim.x;
+          if (i < LL / 4) v[u] = __ldg(s4 + i);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * blockDim.x;
+          if (i < LL / 4) d4[i] = v[u];
+        }
+      }
+    } else {
+      for (int i = threadIdx.x; i < LL; i += blockDim.x) im[i] = __ldg(src + i);
+    }
+  }
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
     twf[i] = g.fwd_tw[i];
     twi[i] = g.inv_tw[i];
@@ -61,10 +87,21 @@ __global__ void __launch_bounds__(kRescoreThreads) rescore_kernel(Geometry g, Re
     const int s = rs % S;
     const int k = rs / S;
     if (warp > 0) {
+      // the sample offsets of eight samples per thread in flight before they are used
       const float2 sh = g.shifts[s];
-      for (int q = threadIdx.x - 32; q < NS; q += blockDim.x - 32) {
-        const float2 o = g.offs[q];
-        samp[q] = bilinear_smem(im, L, c0 + sh.x + o.x, c0 + sh.y + o.y);
+      const int nt = blockDim.x - 32;
+      for (int q0 = threadIdx.x - 32; q0 < NS; q0 += 8 * nt) {
+        float2 o[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u * nt;
+          if (q < NS) o[u] = __ldg(g.offs + q);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u * nt;
+          if (q < NS) samp[q] = bilinear_smem(im, L, c0 + sh.x + o[u].x, c0 + sh.y + o[u].y);
+        }
       }
     }
     __syncthreads();
