@@ -26,6 +26,7 @@
 #include "dev_util.cuh"
 #include "mra_internal.h"
 #include "pair_ifft.cuh"
+#include "smem_limit.cuh"
 #include "tma.cuh"
 
 namespace mra {
@@ -235,13 +236,9 @@ template <int M, int KT>
 static cudaError_t launch_cc_t(const Geometry &g, const CCArgs &a, cudaStream_t st) {
   using Sh = CCShape<M, KT>;
   const size_t smem = Sh::smem(a.seg_max);
-  static size_t attr_set = 0;
-  if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(cc_fp32_kernel<M, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = smem;
-  }
+  static size_t granted = 0;
+  cudaError_t e = raise_smem_limit(cc_fp32_kernel<M, KT>, smem, granted);
+  if (e != cudaSuccess) return e;
   const int64_t row_tiles = (a.rows + Sh::RT - 1) / Sh::RT;
   const int ref_tiles = (a.K + KT - 1) / KT;
   if (row_tiles <= 0) return cudaSuccess;

@@ -7,6 +7,7 @@
 #include "mra_internal.h"
 #include "pair_ifft.cuh"
 #include "ring_fft.cuh"
+#include "smem_limit.cuh"
 
 namespace mra {
 
@@ -224,14 +225,8 @@ size_t rescore_smem(const Geometry &g) {
 // several geometries share the kernel).
 template <int M>
 static cudaError_t rescore_smem_attr(size_t smem) {
-  static size_t attr_set = 0;
-  if (attr_set < smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(rescore_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = smem;
-  }
-  return cudaSuccess;
+  static size_t granted = 0;
+  return raise_smem_limit(rescore_kernel<M>, smem, granted);
 }
 
 template <int M>

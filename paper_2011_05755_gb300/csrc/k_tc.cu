@@ -28,6 +28,7 @@
 #include "mra_internal.h"
 #include "pair_ifft.cuh"
 #include "ring_fft.cuh"
+#include "smem_limit.cuh"
 #include "tma.cuh"
 
 namespace mra {
@@ -869,13 +870,9 @@ template <int M, int KT, bool FP16>
 static cudaError_t launch_tc_t(const Geometry &g, const TcArgs &a, cudaStream_t st) {
   using Sh = TcShape<M, KT>;
   const size_t smem = Sh::smem(a.ks_max);
-  static size_t attr_set = 0;
-  if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(cc_tc_kernel<M, KT, FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = smem;
-  }
+  static size_t granted = 0;
+  cudaError_t e = raise_smem_limit(cc_tc_kernel<M, KT, FP16>, smem, granted);
+  if (e != cudaSuccess) return e;
   const int64_t row_tiles = (a.rows + Sh::RT - 1) / Sh::RT;
   if (row_tiles <= 0) return cudaSuccess;
   dim3 grid((a.K + KT - 1) / KT, static_cast<unsigned>(row_tiles));

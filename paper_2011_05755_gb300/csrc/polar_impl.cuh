@@ -24,6 +24,7 @@
 #include "dev_util.cuh"
 #include "mra_internal.h"
 #include "ring_fft.cuh"
+#include "smem_limit.cuh"
 #include "tma.cuh"
 
 namespace mra {
@@ -359,13 +360,9 @@ __global__ void __launch_bounds__(256, 2) polar_fft_kernel(Geometry g, const __g
 
 template <int R, bool TAPS, int OUT>
 static cudaError_t launch_polar_r(const Geometry &g, const PolarArgs &a, size_t smem, cudaStream_t st) {
-  static size_t attr_set = 0;
-  if (attr_set < smem) {
-    cudaError_t e = cudaFuncSetAttribute(polar_fft_kernel<R, TAPS, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    attr_set = smem;
-  }
+  static size_t granted = 0;
+  cudaError_t e = raise_smem_limit(polar_fft_kernel<R, TAPS, OUT>, smem, granted);
+  if (e != cudaSuccess) return e;
   // CTAs per image (each walks its share of the image's shift groups and
   // stages the image once): four when two or more CTAs fit on an SM, so
   // that the CTAs stay short and the last wave small; one when a CTA fills
