@@ -287,12 +287,14 @@ def main():
     rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
     stream = torch.cuda.current_stream()
 
-    def run_path(prec_code, label, w, refs, imgs, n, steps, warmup):
+    def run_path(prec_code, label, w, refs, imgs, n, steps, warmup, force_kernel=None):
         K, L = w.K, w.L
         rings = ring_table(w.first_ring, w.last_ring, w.ring_step)
         # launch choices of this configuration from the autotuner (timed candidates, cached in JSON)
         from paper_2011_05755_gb300.autotune import tune
-        if args.kernel == "tuned" or prec_code == mra.MRA_FP32:
+        if force_kernel is not None:  # one kernel at the library's default chunking
+            choice = {"kernel": force_kernel, "chunk_images": 0, "candidates": []}
+        elif args.kernel == "tuned" or prec_code == mra.MRA_FP32:
             choice = tune(L, w.first_ring, w.last_ring, w.ring_step, w.shift_range, w.shift_step, w.mirror, prec_code,
                           K)
         else:  # a fixed kernel (profiling runs): the library's default chunking
@@ -460,6 +462,12 @@ def main():
     if not args.no_compare and prec != mra.MRA_FP32:
         cmp_res = run_path(mra.MRA_FP32, "fp32", w, refs, imgs, n, args.steps, args.warmup)
         cmp_res["al"].close()
+    # the same 16-bit step on the tcgen05 contraction kernel (M = 256 only), its own roofline
+    umma_res = None
+    if (not args.no_compare and prec != mra.MRA_FP32 and world == 1 and
+            max(nr for _, nr in ring_table(w.first_ring, w.last_ring, w.ring_step)) == 256):
+        umma_res = run_path(prec, "tcgen05", w, refs, imgs, n, 2, 2, force_kernel=mra.MRA_KERNEL_TCGEN05)
+        umma_res["al"].close()
     al = main_res["al"]
     value, ms_step, prof, roofline, clk, info = (main_res[k] for k in ("value", "ms_step", "prof", "roofline",
                                                                         "clocks", "info"))
@@ -543,6 +551,15 @@ def main():
                                  "gpu_launches": cmp_res["gpu_launches"], "launch": cmp_res["launch"],
                                  "clocks": cmp_res["clocks"],
                                  "step_roofline": cmp_res["step_roofline"]}
+        if umma_res is not None:
+            line["tcgen05_path"] = {"value": umma_res["value"], "ms_per_step": umma_res["ms_step"], "steps": 2,
+                                    "relative_to_headline_path": umma_res["value"] / value,
+                                    "roofline": umma_res["roofline"], "stages": umma_res["prof"],
+                                    "gpu_launches": umma_res["gpu_launches"], "launch": umma_res["launch"],
+                                    "clocks": umma_res["clocks"],
+                                    "note": "the headline step with the tcgen05 / TMEM contraction kernel "
+                                            "(MRA_KERNEL_TCGEN05) at the library's default chunk; the autotuner "
+                                            "keeps mma.sync for the headline where it is faster"}
         print(json.dumps(line), flush=True)
     al.close()
     if world > 1:
